@@ -1,0 +1,163 @@
+/*
+ * bpm.h - C ABI of the B300 split-step beam-propagation library (libbpm.so).
+ *
+ * The library propagates a complex scalar field slice by slice through a
+ * refractive-index volume with the beam-propagation method and the exact
+ * propagator, as in Biobeam (Weigert, Myers & Kreysing, arXiv:1706.02261,
+ * method paragraph), and synthesises the multiplexed focused input fields the
+ * paper introduces in the same paragraph.  For every slice z:
+ *
+ *     E <- IDFT2( H . DFT2(E) ),  H = exp(i kz dz) where kz^2 > 0, else 0,
+ *          kz = sqrt((k0 n0)^2 - kx^2 - ky^2), k0 = 2 pi / lambda
+ *     E <- E . exp(i k0 dn(x, y, z) dz),        dn = n - n0
+ *     I[z] = |E|^2                              (the excitation at every voxel,
+ *                                                light-sheet paragraph)
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
+ *    pointers.  Device arrays must be 16-byte aligned (BPM_ERR_ALIGN otherwise).
+ *  - Fields are interleaved complex float (re, im), row-major [ny][nx]
+ *    (x fastest).  Index volumes are IEEE half dn = n - n0, z-major
+ *    [nz][ny][nx].  Intensity volumes are float, [nz][ny][nx].
+ *  - Lengths are micrometres; lambda is the vacuum wavelength; kx follows the
+ *    DFT bin order 0, 1, ..., then the negative bins; periodic boundaries.
+ *  - Work is enqueued asynchronously on the given stream (0 = legacy default
+ *    stream).  Argument errors are returned immediately; errors found on the
+ *    device (barrier timeout, non-finite index values) are returned by
+ *    bpm_check(), which synchronises the stream of the plan's last call.
+ *  - Every function returns BPM_OK (0) or a negative BPM_ERR_* code and never
+ *    aborts; bpm_last_error() gives a message for the calling thread.
+ *  - A plan may be used from one host thread / one stream at a time.
+ */
+#ifndef BPM_H
+#define BPM_H
+
+#include <stddef.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BPM_OK = 0,
+    BPM_ERR_ARG = -1,          /* invalid argument (size, range, NULL)          */
+    BPM_ERR_ALIGN = -2,        /* a device pointer is not 16-byte aligned       */
+    BPM_ERR_CUDA = -3,         /* a CUDA runtime call failed                    */
+    BPM_ERR_TIMEOUT = -4,      /* a device-side barrier wait ran out of time    */
+    BPM_ERR_NAN = -5,          /* non-finite value in the refractive-index data */
+    BPM_ERR_UNSUPPORTED = -6   /* grid size or configuration not supported      */
+};
+
+/* Plan flags. */
+#define BPM_FLAG_SYNC          0x1u  /* every call synchronises and reports device errors */
+#define BPM_FLAG_MULTI_LAUNCH  0x2u  /* one kernel launch per half-step instead of the
+                                        persistent kernel (comparison path)           */
+
+typedef struct bpm_plan_s *bpm_plan_t;
+
+/* One propagation problem (one field).  Grid sizes nx = ny must be one of
+ * 64, 128, 192, 256, 384, 512, 1024 (products of 2 and 3 the FFT kernels are
+ * built for); nz >= 0.  dx, dy, dz, lambda and n0 must be positive.  tilt_x,
+ * tilt_y are unused by the propagation and reserved for input helpers. */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz, lambda, n0;
+    double tilt_x, tilt_y;
+} bpm_instance_desc;
+
+/* bpm_plan - validate n_inst problem descriptions and build everything the
+ * propagation needs that does not depend on the field: the propagator table
+ * H = exp(i (kz - k0 n0) dz) / (nx ny) per instance (the carrier exp(i k0 n0 dz)
+ * is factored out and applied in FP64 at the end; the 1/(nx ny) of the inverse
+ * DFT is folded in), computed in FP64 on the device and stored as complex
+ * float; the FFT twiddle tables; the team/launch configuration; barrier and
+ * error words.  The plan owns this device memory (about 8 bytes per lateral
+ * pixel per instance plus a few KiB).  The method paragraph of the paper
+ * defines the exact propagator; the evanescent cut maps kz^2 <= 0 to 0.
+ *   out     : receives the plan handle (set to NULL on failure)
+ *   inst    : host array of n_inst descriptions (1 <= n_inst <= 4096)
+ *   flags   : BPM_FLAG_* bits
+ *   stream  : stream on which the table kernels run
+ * Errors: BPM_ERR_ARG, BPM_ERR_UNSUPPORTED, BPM_ERR_CUDA. */
+int bpm_plan(bpm_plan_t *out, const bpm_instance_desc *inst, int n_inst, unsigned flags,
+             cudaStream_t stream);
+
+/* bpm_propagate - run slices [z_begin, z_end) of every instance (clamped to
+ * [0, nz_i)), i.e. the split-step loop of the method paragraph: per slice the
+ * forward 2D DFT, the propagator multiply, the inverse 2D DFT, the phase screen
+ * exp(i k0 dn dz) and the intensity |E|^2.  The whole loop of an instance runs
+ * in one persistent kernel launch (unless BPM_FLAG_MULTI_LAUNCH).
+ *   d_dn   : host array of n_inst device pointers; instance i reads the FP16
+ *            volume [nz_i][ny][nx] (slice z at offset z*nx*ny)
+ *   d_Ein  : host array of device pointers to the input fields (entrance of
+ *            slice z_begin)
+ *   d_Eout : host array of device pointers receiving the field after slice
+ *            z_end-1, including the carrier exp(i k0 n0 dz (z_end - z_begin));
+ *            d_Eout[i] may equal d_Ein[i] (in-place); d_Eout[i] is also the
+ *            working buffer during the call
+ *   d_I    : NULL, or a host array of device pointers (entries may be NULL)
+ *            to [nz_i][ny][nx] float volumes; slice z receives |E|^2 after
+ *            slice z's screen (only slices in [z_begin, z_end) are written)
+ * Errors: BPM_ERR_ARG, BPM_ERR_ALIGN, BPM_ERR_CUDA; device errors via bpm_check. */
+int bpm_propagate(bpm_plan_t p, const void *const *d_dn, const void *const *d_Ein,
+                  void *const *d_Eout, float *const *d_I, int z_begin, int z_end,
+                  cudaStream_t stream);
+
+/* bpm_multiplex_psf - the multiplexed input field of the method paragraph:
+ * the sum of n_foci focused fields, one per emitter.  Emitter j sits at the
+ * grid point nearest to (h_xyz[3j], h_xyz[3j+1]) (rounded in FP64 as
+ * floor(x/dx + 0.5)) with phase h_phase[j], and focuses at depth h_xyz[3j+2]
+ * after forward propagation: its spectrum is cut to the scalar pupil
+ * |k_perp| <= k0 NA (propagating waves only) and multiplied by
+ * exp(-i kz z_j).  Each emitter has amplitude sqrt(nx ny / n_pupil), so each
+ * focused field has unit energy sum |E|^2 = 1 before the summation.  Emitters
+ * sharing a depth are synthesised together (one FFT pair per distinct depth).
+ * Emitters outside the grid are skipped.
+ *   inst   : instance index whose grid is used
+ *   n_foci : 0 <= n_foci <= 1048576
+ *   d_Eout : device [ny][nx] complex float, overwritten
+ * Errors: BPM_ERR_ARG, BPM_ERR_ALIGN, BPM_ERR_CUDA. */
+int bpm_multiplex_psf(bpm_plan_t p, int inst, int n_foci, const double *h_xyz,
+                      const double *h_phase, double NA, void *d_Eout, cudaStream_t stream);
+
+/* bpm_light_sheet - cylindrical light sheet (the paper's Fig. 2a illumination,
+ * NA 0.15): thin along x, uniform along y; angular spectrum
+ * exp(-(kx w0 / 2)^2) on the ky = 0 line, w0 = lambda / (pi NA), centred at
+ * x_c = (nx/2) dx, defocused by exp(-i kz zf) (propagating waves only) and
+ * scaled so that |E|^2 = 1 at (x_c, zf) after exact propagation.
+ *   d_Eout : device [ny][nx] complex float, overwritten
+ * Errors: BPM_ERR_ARG, BPM_ERR_ALIGN, BPM_ERR_CUDA. */
+int bpm_light_sheet(bpm_plan_t p, int inst, double NA, double zf, void *d_Eout,
+                    cudaStream_t stream);
+
+/* bpm_check - wait for the plan's last stream and return the first device
+ * error recorded since the previous bpm_check (BPM_ERR_TIMEOUT, BPM_ERR_NAN),
+ * clearing it; BPM_OK otherwise. */
+int bpm_check(bpm_plan_t p);
+
+/* bpm_free - release the plan's device memory (synchronises its stream).
+ * NULL is accepted.  The handle must not be used afterwards. */
+int bpm_free(bpm_plan_t p);
+
+/* bpm_last_error - message for the last failing call on this host thread. */
+const char *bpm_last_error(void);
+
+/* bpm_plan_info - launch configuration chosen for the plan, for reports:
+ * out[0] = team CTAs, out[1] = threads per CTA, out[2] = dynamic shared
+ * memory bytes, out[3] = persistent (1) or multi-launch (0), out[4] = kernel
+ * launches per bpm_propagate call. */
+int bpm_plan_info(bpm_plan_t p, int *out, int n_out);
+
+/* bpm_debug_set_barrier_timeout - test hook: device barrier wait limit in
+ * nanoseconds for this plan (default 2e9), and an extra count added to the
+ * barrier target so that a barrier can be made to run out on purpose (0 in
+ * normal use).  A barrier that runs out records BPM_ERR_TIMEOUT and every CTA
+ * leaves the kernel. */
+int bpm_debug_set_barrier_timeout(bpm_plan_t p, unsigned long long timeout_ns,
+                                  unsigned extra_arrivals);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BPM_H */

@@ -36,7 +36,7 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile ``bpm_oracle.c`` into ``liboracle.so`` with gcc (FP64, OpenMP)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11",
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=gnu11",
                "-Wall", _SRC, "-o", _LIB_PATH, "-lm"]
         subprocess.run(cmd, check=True)
     return _LIB_PATH

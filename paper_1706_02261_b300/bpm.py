@@ -1,0 +1,177 @@
+"""Python binding of libbpm.so (include/bpm.h): argument marshalling only.
+
+Every function mirrors the C entry point of the same name; device buffers are
+torch CUDA tensors (complex64 fields, float16 index volumes, float32 intensity
+volumes) and streams are torch CUDA streams.  All arithmetic runs in the
+library's CUDA kernels; when the library is missing this module raises on
+import rather than falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbpm.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "bpm.h")
+
+BPM_OK = 0
+BPM_ERR_ARG = -1
+BPM_ERR_ALIGN = -2
+BPM_ERR_CUDA = -3
+BPM_ERR_TIMEOUT = -4
+BPM_ERR_NAN = -5
+BPM_ERR_UNSUPPORTED = -6
+BPM_FLAG_SYNC = 0x1
+BPM_FLAG_MULTI_LAUNCH = 0x2
+
+SUPPORTED_N = (64, 128, 192, 256, 384, 512, 1024)
+
+
+class BpmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class bpm_instance_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("n0", ctypes.c_double),
+                ("tilt_x", ctypes.c_double), ("tilt_y", ctypes.c_double)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libbpm.so not found at {LIB_PATH}; build it with "
+                      f"`python -m paper_1706_02261_b300.build` (nvcc, sm_103a)")
+_lib = ctypes.CDLL(LIB_PATH)
+_vp, _i, _u, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double
+_pp = ctypes.POINTER(ctypes.c_void_p)
+_lib.bpm_plan.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(bpm_instance_desc), _i, _u, _vp]
+_lib.bpm_propagate.argtypes = [_vp, _pp, _pp, _pp, _pp, _i, _i, _vp]
+_lib.bpm_multiplex_psf.argtypes = [_vp, _i, _i, _vp, _vp, _d, _vp, _vp]
+_lib.bpm_light_sheet.argtypes = [_vp, _i, _d, _d, _vp, _vp]
+_lib.bpm_check.argtypes = [_vp]
+_lib.bpm_free.argtypes = [_vp]
+_lib.bpm_last_error.restype = ctypes.c_char_p
+_lib.bpm_plan_info.argtypes = [_vp, ctypes.POINTER(_i), _i]
+_lib.bpm_debug_set_barrier_timeout.argtypes = [_vp, ctypes.c_ulonglong, _u]
+for _f in ("bpm_plan", "bpm_propagate", "bpm_multiplex_psf", "bpm_light_sheet", "bpm_check",
+           "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout"):
+    getattr(_lib, _f).restype = _i
+
+
+def declared_symbols() -> list:
+    """Names of the functions declared in include/bpm.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:int|const char \*)\s*(bpm_\w+)\s*\(", txt, re.M)))
+
+
+def library() -> ctypes.CDLL:
+    return _lib
+
+
+def bpm_last_error() -> str:
+    return _lib.bpm_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != BPM_OK:
+        raise BpmError(rc, bpm_last_error())
+    return rc
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _arr(ptrs):
+    a = (ctypes.c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        a[i] = p.value if isinstance(p, ctypes.c_void_p) else p
+    return a
+
+
+@dataclass
+class Instance:
+    """One propagation problem (grid, spacings in um, vacuum wavelength, n0)."""
+    n: int
+    nz: int
+    dx: float
+    dz: float
+    lam: float = 0.5
+    n0: float = 1.33
+    dy: float | None = None
+
+    def desc(self) -> bpm_instance_desc:
+        return bpm_instance_desc(self.n, self.n, self.nz, self.dx, self.dy or self.dx, self.dz,
+                                 self.lam, self.n0, 0.0, 0.0)
+
+
+def bpm_plan(instances, flags: int = 0, stream=None) -> ctypes.c_void_p:
+    if isinstance(instances, Instance):
+        instances = [instances]
+    descs = (bpm_instance_desc * len(instances))(*[i.desc() for i in instances])
+    h = ctypes.c_void_p()
+    _check(_lib.bpm_plan(ctypes.byref(h), descs, len(instances), flags, _stream_handle(stream)))
+    return h
+
+
+def bpm_propagate(plan, dn, e_in, e_out, inten=None, z_begin: int = 0, z_end: int = 2 ** 31 - 1,
+                  stream=None) -> int:
+    """dn, e_in, e_out, inten: tensors or lists of tensors (one per instance)."""
+    single = not isinstance(e_in, (list, tuple))
+    dn, e_in, e_out = ([dn], [e_in], [e_out]) if single else (dn, e_in, e_out)
+    if inten is not None and single:
+        inten = [inten]
+    a_dn = _arr([_ptr(t) or ctypes.c_void_p(0) for t in dn])
+    a_in = _arr([_ptr(t) for t in e_in])
+    a_out = _arr([_ptr(t) for t in e_out])
+    a_i = _arr([_ptr(t) if t is not None else ctypes.c_void_p(0) for t in inten]) if inten is not None else None
+    return _check(_lib.bpm_propagate(plan, a_dn, a_in, a_out, a_i, z_begin, z_end, _stream_handle(stream)))
+
+
+def bpm_multiplex_psf(plan, inst: int, xyz: np.ndarray, phase: np.ndarray, NA: float, e_out,
+                      stream=None) -> int:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    phase = np.ascontiguousarray(phase, dtype=np.float64).reshape(-1)
+    assert phase.size == xyz.shape[0]
+    return _check(_lib.bpm_multiplex_psf(plan, inst, phase.size, ctypes.c_void_p(xyz.ctypes.data),
+                                         ctypes.c_void_p(phase.ctypes.data), NA, _ptr(e_out),
+                                         _stream_handle(stream)))
+
+
+def bpm_light_sheet(plan, inst: int, NA: float, zf: float, e_out, stream=None) -> int:
+    return _check(_lib.bpm_light_sheet(plan, inst, NA, zf, _ptr(e_out), _stream_handle(stream)))
+
+
+def bpm_check(plan) -> int:
+    return _lib.bpm_check(plan)
+
+
+def bpm_free(plan) -> int:
+    return _check(_lib.bpm_free(plan))
+
+
+def bpm_plan_info(plan) -> dict:
+    out = (ctypes.c_int * 5)()
+    _check(_lib.bpm_plan_info(plan, out, 5))
+    return {"team_ctas": out[0], "threads": out[1], "smem_bytes": out[2], "persistent": out[3],
+            "launches_per_call": out[4]}
+
+
+def bpm_debug_set_barrier_timeout(plan, timeout_ns: int, extra_arrivals: int = 0) -> int:
+    return _check(_lib.bpm_debug_set_barrier_timeout(plan, timeout_ns, extra_arrivals))

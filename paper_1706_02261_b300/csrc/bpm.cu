@@ -1,0 +1,553 @@
+// bpm.cu - host side of libbpm.so: plans, launches and the C ABI of bpm.h.
+//
+// Plans validate problem descriptions, build the FP64 propagator tables and the
+// FFT twiddle tables on the device, and pick the team (number of CTAs that
+// share one field).  Propagation is one cooperative persistent launch per
+// instance: the team loops over all slices with two device-wide barriers per
+// slice (see bpm_kernels.cuh).  Every entry point returns a status code and
+// records a message for bpm_last_error().
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bpm.h"
+#include "bpm_kernels.cuh"
+
+using namespace bpmk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define BPM_CU(call)                                                                     \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(BPM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+  } while (0)
+
+constexpr double kTwoPi = 6.283185307179586;
+
+bool supported_n(int n) {
+  switch (n) {
+    case 64: case 128: case 192: case 256: case 384: case 512: case 1024: return true;
+    default: return false;
+  }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Host-built twiddle table of one transform (FP64, rounded once): for every
+// pass p >= 1 of the radix list, N entries laid out [b][r][t] holding
+// W_{Ns R}^{(j mod Ns) r}, j = t + b T, with the transform's sign.
+void append_twiddles(std::vector<float2>& out, int N, int T, const std::vector<int>& radices, int sign) {
+  int Ns = 1;
+  for (size_t p = 0; p < radices.size(); ++p) {
+    const int R = radices[p];
+    if (p > 0) {
+      const int B = N / (R * T);
+      const size_t base = out.size();
+      out.resize(base + (size_t)N);
+      for (int b = 0; b < B; ++b)
+        for (int r = 0; r < R; ++r)
+          for (int t = 0; t < T; ++t) {
+            const int j = t + b * T;
+            const long long e = (long long)(j % Ns) * r % (long long)(Ns * R);
+            const double ang = sign * kTwoPi * (double)e / (double)(Ns * R);
+            out[base + (size_t)(b * R + r) * T + t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+          }
+    }
+    Ns *= R;
+  }
+}
+
+template <class RS>
+std::vector<int> radix_list() {
+  std::vector<int> r;
+  for (int i = 0; i < RS::count; ++i) r.push_back(RS::at(i));
+  return r;
+}
+
+template <int N>
+std::vector<float2> twiddles_for() {
+  using C = Cfg<N>;
+  std::vector<float2> v;
+  if constexpr (C::kLoop) {
+    append_twiddles(v, N, C::T, std::vector<int>(C::E::NP, C::E::R), -1);
+  } else {
+    append_twiddles(v, N, C::T, radix_list<typename C::F::Rad>(), -1);
+    append_twiddles(v, N, C::T, radix_list<typename C::I::Rad>(), +1);
+  }
+  return v;
+}
+
+}  // namespace
+
+struct NRes {
+  int n = 0;
+  float2* tw = nullptr;
+  float2* tmp = nullptr;    // N x N scratch for input synthesis (allocated on first use)
+  int team = 0;             // CTAs per field
+  size_t smem = 0;          // dynamic shared memory of the half-step kernels
+  size_t smem_persist = 0;  // ... of the persistent kernel (with its staging buffers)
+  int rmax = 0;             // rows (= columns) per team CTA at most
+  int h_res = 0, dn_stage = 0, i_stage = 0;
+};
+
+struct InstPlan {
+  bpm_instance_desc d;
+  float2* ht = nullptr;
+};
+
+struct bpm_plan_s {
+  std::vector<InstPlan> inst;
+  std::map<int, NRes> res;
+  unsigned flags = 0;
+  int dev = 0, sms = 0;
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  unsigned long long* npupil = nullptr;
+  int* foci_idx = nullptr;
+  double* foci_phase = nullptr;
+  int foci_cap = 0;
+  unsigned long long timeout_ns = 2000000000ull;
+  unsigned bar_extra = 0;
+  cudaStream_t last = 0;
+};
+
+namespace {
+
+template <int N>
+int setup_kernels(NRes& r, int sms) {
+  using C = Cfg<N>;
+  r.smem = C::smem_bytes();
+  const int smem = (int)r.smem;
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_INV_ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_col_kernel<N, COL_PROP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_col_kernel<N, COL_FOCUS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_light_sheet_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem + (int)(C::GS * sizeof(float2))));
+  // smallest team that gives every group one row per half-step, at most one CTA per SM
+  const int want = (N + C::NG - 1) / C::NG;
+  r.team = std::max(1, std::min(want, sms));
+  // staging buffers of the persistent kernel, dropped (propagator columns
+  // first) if they would not fit next to the group buffers
+  int max_optin = 0;
+  BPM_CU(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
+  r.rmax = (N + r.team - 1) / r.team;
+  auto rup = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  const size_t hb = rup((size_t)r.rmax * N * sizeof(float2)), db = rup((size_t)r.rmax * N * 2),
+               ib = rup((size_t)r.rmax * N * sizeof(float));
+  const size_t budget = (size_t)max_optin - 1024;   // static shared memory of the kernel
+  r.h_res = r.dn_stage = r.i_stage = 1;
+  if (r.smem + hb + db + ib > budget) r.h_res = 0;
+  if (r.smem + db + ib > budget) r.i_stage = 0;
+  if (r.smem + db > budget) r.dn_stage = 0;
+  r.smem_persist = r.smem + (r.h_res ? hb : 0) + (r.dn_stage ? db : 0) + (r.i_stage ? ib : 0);
+  BPM_CU(cudaFuncSetAttribute(bpm_persistent_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)r.smem_persist));
+  int per_sm = 0;
+  BPM_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpm_persistent_kernel<N>, kThreads,
+                                                       r.smem_persist));
+  if (per_sm < 1) return fail(BPM_ERR_UNSUPPORTED, "persistent kernel for N=%d does not fit on an SM", N);
+  std::vector<float2> tw = twiddles_for<N>();
+  if (tw.size() != (size_t)(C::TWF + C::TWI) || tw.empty())
+    return fail(BPM_ERR_UNSUPPORTED, "twiddle table size mismatch for N=%d", N);
+  BPM_CU(cudaMalloc(&r.tw, tw.size() * sizeof(float2)));
+  BPM_CU(cudaMemcpy(r.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  return BPM_OK;
+}
+
+int setup_n(NRes& r, int n, int sms) {
+  r.n = n;
+  switch (n) {
+    case 64: return setup_kernels<64>(r, sms);
+    case 128: return setup_kernels<128>(r, sms);
+    case 192: return setup_kernels<192>(r, sms);
+    case 256: return setup_kernels<256>(r, sms);
+    case 384: return setup_kernels<384>(r, sms);
+    case 512: return setup_kernels<512>(r, sms);
+    case 1024: return setup_kernels<1024>(r, sms);
+  }
+  return fail(BPM_ERR_UNSUPPORTED, "grid size %d is not supported", n);
+}
+
+int check_desc(const bpm_instance_desc& d, int i) {
+  if (d.nx != d.ny)
+    return fail(BPM_ERR_UNSUPPORTED, "instance %d: nx (%d) != ny (%d) is not supported", i, d.nx, d.ny);
+  if (!supported_n(d.nx))
+    return fail(BPM_ERR_UNSUPPORTED, "instance %d: nx = %d is not one of 64,128,192,256,384,512,1024", i, d.nx);
+  if (d.nz < 0) return fail(BPM_ERR_ARG, "instance %d: nz < 0", i);
+  if (!(d.dx > 0) || !(d.dy > 0) || !(d.dz > 0) || !(d.lambda > 0) || !(d.n0 > 0) || !std::isfinite(d.dx) ||
+      !std::isfinite(d.dy) || !std::isfinite(d.dz) || !std::isfinite(d.lambda) || !std::isfinite(d.n0))
+    return fail(BPM_ERR_ARG, "instance %d: dx, dy, dz, lambda and n0 must be positive and finite", i);
+  return BPM_OK;
+}
+
+void free_plan(bpm_plan_s* p) {
+  if (!p) return;
+  for (auto& in : p->inst) cudaFree(in.ht);
+  for (auto& kv : p->res) {
+    cudaFree(kv.second.tw);
+    cudaFree(kv.second.tmp);
+  }
+  cudaFree(p->bar);
+  cudaFree(p->err);
+  cudaFree(p->npupil);
+  cudaFree(p->foci_idx);
+  cudaFree(p->foci_phase);
+  delete p;
+}
+
+StepArgs base_args(bpm_plan_s* p, const InstPlan& in, const NRes& r) {
+  StepArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.ht = in.ht;
+  a.tw = r.tw;
+  const double k0 = kTwoPi / in.d.lambda;
+  a.screen_c = (float)(k0 * in.d.dz);
+  a.k0n0 = k0 * in.d.n0;
+  a.dx = in.d.dx;
+  a.dy = in.d.dy;
+  a.bar = p->bar;
+  a.err = p->err;
+  a.timeout_ns = p->timeout_ns;
+  a.bar_extra = p->bar_extra;
+  a.carrier = make_float2(1.f, 0.f);
+  a.rmax = r.rmax;
+  a.h_res = r.h_res;
+  a.dn_stage = r.dn_stage;
+  a.i_stage = r.i_stage;
+  return a;
+}
+
+// ---- launches ---------------------------------------------------------------
+
+template <int N>
+int launch_propagate(bpm_plan_s* p, const NRes& r, StepArgs a, cudaStream_t s) {
+  const int G = r.team;
+  if (p->flags & BPM_FLAG_MULTI_LAUNCH) {
+    bpm_row_kernel<N, ROW_FWD><<<G, kThreads, r.smem, s>>>(a, a.z_begin);
+    for (int z = a.z_begin; z < a.z_end; ++z) {
+      bpm_col_kernel<N, COL_PROP><<<G, kThreads, r.smem, s>>>(a);
+      if (z + 1 < a.z_end) bpm_row_kernel<N, ROW_STEP><<<G, kThreads, r.smem, s>>>(a, z);
+      else bpm_row_kernel<N, ROW_LAST><<<G, kThreads, r.smem, s>>>(a, z);
+    }
+    BPM_CU(cudaGetLastError());
+    return BPM_OK;
+  }
+  BPM_CU(cudaMemsetAsync(p->bar, 0, sizeof(unsigned), s));
+  void* args[] = {&a};
+  BPM_CU(cudaLaunchCooperativeKernel((const void*)bpm_persistent_kernel<N>, dim3(G), dim3(kThreads), args,
+                                     r.smem_persist, s));
+  return BPM_OK;
+}
+
+template <int N>
+int launch_synth_group(bpm_plan_s*, const NRes& r, StepArgs a, cudaStream_t s) {
+  const int G = r.team;
+  bpm_row_kernel<N, ROW_FWD><<<G, kThreads, r.smem, s>>>(a, 0);
+  bpm_col_kernel<N, COL_FOCUS><<<G, kThreads, r.smem, s>>>(a);
+  bpm_row_kernel<N, ROW_INV_ACC><<<G, kThreads, r.smem, s>>>(a, 0);
+  BPM_CU(cudaGetLastError());
+  return BPM_OK;
+}
+
+template <int N>
+int launch_light_sheet(bpm_plan_s* p, const NRes& r, StepArgs a, double w0, double xc, cudaStream_t s) {
+  using C = Cfg<N>;
+  const int grid = std::max(1, std::min(p->sms, (N * N + 4 * kThreads - 1) / (4 * kThreads)));
+  bpm_light_sheet_kernel<N><<<grid, kThreads, r.smem + C::GS * sizeof(float2), s>>>(a, w0, xc);
+  BPM_CU(cudaGetLastError());
+  return BPM_OK;
+}
+
+#define BPM_DISPATCH(n, call)                               \
+  switch (n) {                                              \
+    case 64: { constexpr int N = 64; return call; }         \
+    case 128: { constexpr int N = 128; return call; }       \
+    case 192: { constexpr int N = 192; return call; }       \
+    case 256: { constexpr int N = 256; return call; }       \
+    case 384: { constexpr int N = 384; return call; }       \
+    case 512: { constexpr int N = 512; return call; }       \
+    case 1024: { constexpr int N = 1024; return call; }     \
+  }                                                         \
+  return fail(BPM_ERR_UNSUPPORTED, "grid size %d is not supported", n);
+
+int dispatch_propagate(bpm_plan_s* p, const NRes& r, const StepArgs& a, cudaStream_t s) {
+  BPM_DISPATCH(r.n, launch_propagate<N>(p, r, a, s))
+}
+int dispatch_synth(bpm_plan_s* p, const NRes& r, const StepArgs& a, cudaStream_t s) {
+  BPM_DISPATCH(r.n, launch_synth_group<N>(p, r, a, s))
+}
+int dispatch_light_sheet(bpm_plan_s* p, const NRes& r, const StepArgs& a, double w0, double xc, cudaStream_t s) {
+  BPM_DISPATCH(r.n, launch_light_sheet<N>(p, r, a, w0, xc, s))
+}
+
+int finish_call(bpm_plan_s* p, cudaStream_t s) {
+  p->last = s;
+  if (p->flags & BPM_FLAG_SYNC) return bpm_check(p);
+  return BPM_OK;
+}
+
+}  // namespace
+
+// ---- C ABI -------------------------------------------------------------------
+
+extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_inst, unsigned flags,
+                        cudaStream_t stream) {
+  if (!out) return fail(BPM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!inst || n_inst < 1 || n_inst > 4096) return fail(BPM_ERR_ARG, "n_inst must be in [1, 4096]");
+  if (flags & ~(BPM_FLAG_SYNC | BPM_FLAG_MULTI_LAUNCH)) return fail(BPM_ERR_ARG, "unknown flag bits 0x%x", flags);
+  for (int i = 0; i < n_inst; ++i) {
+    int rc = check_desc(inst[i], i);
+    if (rc) return rc;
+  }
+  bpm_plan_s* p = new (std::nothrow) bpm_plan_s;
+  if (!p) return fail(BPM_ERR_ARG, "out of host memory");
+  p->flags = flags;
+  int rc = BPM_OK;
+  auto cu = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && rc == BPM_OK) rc = fail(BPM_ERR_CUDA, "%s failed: %s", what, cudaGetErrorString(e));
+    return e == cudaSuccess;
+  };
+  cu(cudaGetDevice(&p->dev), "cudaGetDevice");
+  if (rc == BPM_OK) cu(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->dev), "cudaDeviceGetAttribute");
+  if (rc == BPM_OK) cu(cudaMalloc(&p->bar, 64), "cudaMalloc(barrier)");
+  if (rc == BPM_OK) cu(cudaMalloc(&p->err, sizeof(int)), "cudaMalloc(error word)");
+  if (rc == BPM_OK) cu(cudaMalloc(&p->npupil, sizeof(unsigned long long)), "cudaMalloc(pupil count)");
+  if (rc == BPM_OK) cu(cudaMemset(p->err, 0, sizeof(int)), "cudaMemset");
+  for (int i = 0; i < n_inst && rc == BPM_OK; ++i) {
+    InstPlan ip;
+    ip.d = inst[i];
+    const int n = inst[i].nx;
+    if (!p->res.count(n)) {
+      NRes r;
+      rc = setup_n(r, n, p->sms);
+      p->res[n] = r;
+      if (rc) break;
+    }
+    const size_t M = (size_t)n * n;
+    if (!cu(cudaMalloc(&ip.ht, M * sizeof(float2)), "cudaMalloc(propagator)")) break;
+    p->inst.push_back(ip);
+    const int threads = 256;
+    bpm_build_ht_kernel<<<(unsigned)((M + threads - 1) / threads), threads, 0, stream>>>(
+        ip.ht, inst[i].nx, inst[i].ny, inst[i].dx, inst[i].dy, inst[i].dz, inst[i].lambda, inst[i].n0);
+    cu(cudaGetLastError(), "bpm_build_ht_kernel");
+  }
+  if (rc == BPM_OK) cu(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+  if (rc != BPM_OK) {
+    free_plan(p);
+    return rc;
+  }
+  p->last = stream;
+  *out = p;
+  return BPM_OK;
+}
+
+extern "C" int bpm_propagate(bpm_plan_t p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
+                             float* const* d_I, int z_begin, int z_end, cudaStream_t stream) {
+  if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
+  if (!d_dn || !d_Ein || !d_Eout) return fail(BPM_ERR_ARG, "d_dn, d_Ein and d_Eout must be non-NULL arrays");
+  if (z_begin < 0 || z_end < z_begin) return fail(BPM_ERR_ARG, "need 0 <= z_begin <= z_end");
+  for (size_t i = 0; i < p->inst.size(); ++i) {
+    const InstPlan& in = p->inst[i];
+    const int zb = std::min(z_begin, in.d.nz), ze = std::min(z_end, in.d.nz);
+    if (!d_Ein[i] || !d_Eout[i] || (ze > zb && !d_dn[i]))
+      return fail(BPM_ERR_ARG, "instance %zu: NULL device pointer", i);
+    if (!aligned16(d_Ein[i]) || !aligned16(d_Eout[i]) || !aligned16(d_dn[i]) || (d_I && !aligned16(d_I[i])))
+      return fail(BPM_ERR_ALIGN, "instance %zu: device pointers must be 16-byte aligned", i);
+  }
+  for (size_t i = 0; i < p->inst.size(); ++i) {
+    const InstPlan& in = p->inst[i];
+    const NRes& r = p->res[in.d.nx];
+    const int zb = std::min(z_begin, in.d.nz), ze = std::min(z_end, in.d.nz);
+    const size_t bytes = (size_t)in.d.nx * in.d.ny * sizeof(float2);
+    if (ze == zb) {
+      if (d_Eout[i] != d_Ein[i])
+        BPM_CU(cudaMemcpyAsync(d_Eout[i], d_Ein[i], bytes, cudaMemcpyDeviceToDevice, stream));
+      continue;
+    }
+    StepArgs a = base_args(p, in, r);
+    a.work = static_cast<float2*>(d_Eout[i]);
+    a.ein = static_cast<const float2*>(d_Ein[i]);
+    a.dn = static_cast<const __half*>(d_dn[i]);
+    a.inten = d_I ? d_I[i] : nullptr;
+    a.z_begin = zb;
+    a.z_end = ze;
+    const double k0 = kTwoPi / in.d.lambda;
+    double ph = std::fmod(k0 * in.d.n0 * in.d.dz * (double)(ze - zb), kTwoPi);
+    a.carrier = make_float2((float)std::cos(ph), (float)std::sin(ph));
+    int rc = dispatch_propagate(p, r, a, stream);
+    if (rc) return rc;
+  }
+  return finish_call(p, stream);
+}
+
+extern "C" int bpm_multiplex_psf(bpm_plan_t p, int inst, int n_foci, const double* h_xyz, const double* h_phase,
+                                 double NA, void* d_Eout, cudaStream_t stream) {
+  if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
+  if (inst < 0 || inst >= (int)p->inst.size()) return fail(BPM_ERR_ARG, "instance %d out of range", inst);
+  if (n_foci < 0 || n_foci > (1 << 20)) return fail(BPM_ERR_ARG, "n_foci must be in [0, 1048576]");
+  if (n_foci > 0 && (!h_xyz || !h_phase)) return fail(BPM_ERR_ARG, "h_xyz and h_phase must be non-NULL");
+  if (!(NA > 0) || !std::isfinite(NA)) return fail(BPM_ERR_ARG, "NA must be positive");
+  if (!d_Eout) return fail(BPM_ERR_ARG, "d_Eout is NULL");
+  if (!aligned16(d_Eout)) return fail(BPM_ERR_ALIGN, "d_Eout must be 16-byte aligned");
+  const InstPlan& in = p->inst[inst];
+  NRes& r = p->res[in.d.nx];
+  const int n = in.d.nx;
+  const size_t M = (size_t)n * n;
+  // emitters on the grid, grouped by focal depth (stable order within a group)
+  std::vector<int> order;
+  for (int j = 0; j < n_foci; ++j) {
+    const double x = h_xyz[3 * j], y = h_xyz[3 * j + 1], z = h_xyz[3 * j + 2];
+    if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z) || !std::isfinite(h_phase[j]))
+      return fail(BPM_ERR_ARG, "emitter %d has a non-finite coordinate or phase", j);
+    const double fx = std::floor(x / in.d.dx + 0.5), fy = std::floor(y / in.d.dy + 0.5);
+    if (fx < 0 || fx >= n || fy < 0 || fy >= n) continue;
+    order.push_back(j);
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return h_xyz[3 * a + 2] < h_xyz[3 * b + 2]; });
+  if (order.empty()) {
+    BPM_CU(cudaMemsetAsync(d_Eout, 0, M * sizeof(float2), stream));
+    return finish_call(p, stream);
+  }
+  if ((int)order.size() > p->foci_cap) {
+    BPM_CU(cudaStreamSynchronize(stream));
+    cudaFree(p->foci_idx);
+    cudaFree(p->foci_phase);
+    p->foci_idx = nullptr;
+    p->foci_phase = nullptr;
+    p->foci_cap = 0;
+    BPM_CU(cudaMalloc(&p->foci_idx, order.size() * sizeof(int)));
+    BPM_CU(cudaMalloc(&p->foci_phase, order.size() * sizeof(double)));
+    p->foci_cap = (int)order.size();
+  }
+  if (!r.tmp) BPM_CU(cudaMalloc(&r.tmp, M * sizeof(float2)));
+  std::vector<int> idx;
+  std::vector<double> ph, zs;
+  for (int j : order) {
+    const int fx = (int)std::floor(h_xyz[3 * j] / in.d.dx + 0.5);
+    const int fy = (int)std::floor(h_xyz[3 * j + 1] / in.d.dy + 0.5);
+    idx.push_back(fy * n + fx);
+    ph.push_back(h_phase[j]);
+    zs.push_back(h_xyz[3 * j + 2]);
+  }
+  // device staging of the emitter lists (pageable source: the copy completes
+  // before cudaMemcpyAsync returns, so the host vectors may go out of scope)
+  BPM_CU(cudaMemcpyAsync(p->foci_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+  BPM_CU(cudaMemcpyAsync(p->foci_phase, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice, stream));
+  const double k0 = kTwoPi / in.d.lambda;
+  const double kna = k0 * NA;
+  StepArgs a = base_args(p, in, r);
+  a.kna2 = kna * kna;
+  BPM_CU(cudaMemsetAsync(p->npupil, 0, sizeof(unsigned long long), stream));
+  bpm_pupil_count_kernel<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>(n, in.d.dx, in.d.dy, a.k0n0, a.kna2,
+                                                                         p->npupil);
+  BPM_CU(cudaGetLastError());
+  size_t g0 = 0;
+  int group = 0;
+  while (g0 < idx.size()) {
+    size_t g1 = g0;
+    while (g1 < idx.size() && zs[g1] == zs[g0]) ++g1;
+    BPM_CU(cudaMemsetAsync(r.tmp, 0, M * sizeof(float2), stream));
+    const int cnt = (int)(g1 - g0);
+    bpm_scatter_kernel<<<(cnt + 127) / 128, 128, 0, stream>>>(r.tmp, n, p->foci_idx + g0, p->foci_phase + g0, cnt,
+                                                              p->npupil);
+    BPM_CU(cudaGetLastError());
+    a.work = r.tmp;
+    a.ein = r.tmp;
+    a.out = static_cast<float2*>(d_Eout);
+    a.zf = zs[g0];
+    a.accumulate = group > 0;
+    int rc = dispatch_synth(p, r, a, stream);
+    if (rc) return rc;
+    g0 = g1;
+    ++group;
+  }
+  return finish_call(p, stream);
+}
+
+extern "C" int bpm_light_sheet(bpm_plan_t p, int inst, double NA, double zf, void* d_Eout, cudaStream_t stream) {
+  if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
+  if (inst < 0 || inst >= (int)p->inst.size()) return fail(BPM_ERR_ARG, "instance %d out of range", inst);
+  if (!(NA > 0) || !std::isfinite(NA) || !std::isfinite(zf)) return fail(BPM_ERR_ARG, "NA must be positive, zf finite");
+  if (!d_Eout) return fail(BPM_ERR_ARG, "d_Eout is NULL");
+  if (!aligned16(d_Eout)) return fail(BPM_ERR_ALIGN, "d_Eout must be 16-byte aligned");
+  const InstPlan& in = p->inst[inst];
+  const NRes& r = p->res[in.d.nx];
+  StepArgs a = base_args(p, in, r);
+  a.work = static_cast<float2*>(d_Eout);
+  a.zf = zf;
+  const double w0 = in.d.lambda / (M_PI * NA);
+  const double xc = (double)(in.d.nx / 2) * in.d.dx;
+  int rc = dispatch_light_sheet(p, r, a, w0, xc, stream);
+  if (rc) return rc;
+  return finish_call(p, stream);
+}
+
+extern "C" int bpm_check(bpm_plan_t p) {
+  if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
+  BPM_CU(cudaStreamSynchronize(p->last));
+  BPM_CU(cudaGetLastError());
+  int e = 0;
+  BPM_CU(cudaMemcpy(&e, p->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    BPM_CU(cudaMemset(p->err, 0, sizeof(int)));
+    if (e == BPM_ERR_TIMEOUT) return fail(BPM_ERR_TIMEOUT, "a device barrier wait ran out of time");
+    if (e == BPM_ERR_NAN) return fail(BPM_ERR_NAN, "non-finite value in the refractive-index volume");
+    return fail(e, "device error %d", e);
+  }
+  return BPM_OK;
+}
+
+extern "C" int bpm_free(bpm_plan_t p) {
+  if (!p) return BPM_OK;
+  cudaStreamSynchronize(p->last);
+  free_plan(p);
+  return BPM_OK;
+}
+
+extern "C" const char* bpm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int bpm_plan_info(bpm_plan_t p, int* out, int n_out) {
+  if (!p || !out || n_out < 0) return fail(BPM_ERR_ARG, "bad arguments");
+  const NRes& r = p->res.begin()->second;
+  const bool multi = (p->flags & BPM_FLAG_MULTI_LAUNCH) != 0;
+  const int nz = p->inst[0].d.nz;
+  int vals[5] = {r.team, kThreads, (int)(multi ? r.smem : r.smem_persist), multi ? 0 : 1, multi ? 1 + 2 * nz : 1};
+  for (int i = 0; i < n_out && i < 5; ++i) out[i] = vals[i];
+  return BPM_OK;
+}
+
+extern "C" int bpm_debug_set_barrier_timeout(bpm_plan_t p, unsigned long long timeout_ns, unsigned extra) {
+  if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
+  if (timeout_ns == 0) return fail(BPM_ERR_ARG, "timeout must be positive");
+  p->timeout_ns = timeout_ns;
+  p->bar_extra = extra;
+  return BPM_OK;
+}

@@ -1,0 +1,786 @@
+// bpm_kernels.cuh - device side of the split-step beam-propagation library.
+//
+// A "team" of CTAs owns one field of N x N complex floats that lives in global
+// memory (L2-resident: 8 MiB at N = 1024).  Each slice of the method is two
+// half-steps separated by team-wide barriers:
+//
+//   column half-step  (CTA owns a block of columns):
+//       stage its columns in shared memory, FFT_y, multiply by the propagator
+//       column H^T[kx][:], inverse FFT_y, write the columns back;
+//   row half-step     (CTA owns a block of rows):
+//       inverse FFT_x, phase screen exp(i k0 dn dz) from the FP16 dn row,
+//       |E|^2 to the intensity volume, then the forward FFT_x of the next
+//       slice (or the FP64 carrier on the last slice), write the row back.
+//
+// The forward FFT_x of the first slice is a row half-step of its own.  Row
+// and column transforms run in registers (see fft.cuh) with one shared-memory
+// exchange per radix pass.  The 2D DFT needs all rows before any column, so
+// two team barriers per slice are the minimum for one field.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace bpmk {
+
+constexpr int kThreads = 256;   // CTA size for every kernel of the path
+constexpr int kWarps = kThreads / 32;
+
+// device error codes (match the negative BPM_ERR_* values of bpm.h)
+constexpr int kDevErrTimeout = -4;
+constexpr int kDevErrNan = -5;
+
+// Per-N transform configuration.  Two engines:
+//  - LoopCfg: N = R^P with one radix R; a rolled pass loop (LoopFFT) and the
+//    inverse by conjugation, so a half-step is one compact loop over 2P passes
+//    with the pointwise operation (propagator or screen) in the middle.
+//  - GroupCfg: mixed radices (products with 3, or 2^7) through the unrolled
+//    GroupFFT with separate forward and inverse schedules.
+// Both expose: T threads per row, the register layouts L(R0) (natural order,
+// forward input / inverse output) and L(RL) (spectrum order, forward output /
+// inverse input), the shared-memory index map f, the group stride GS (chosen
+// so that FFT exchanges and column staging are free of bank conflicts for the
+// power-of-two sizes) and the twiddle table lengths.
+template <int N_, int T_, int GS_>
+struct CfgBase {
+  static constexpr int N = N_, T = T_, GS = GS_;
+  static constexpr int PTS = N_ / T_;
+  static constexpr int GPW = 32 / T_;
+  static constexpr int NG = kWarps * GPW;   // row/column groups per CTA
+};
+
+template <int N_, int T_, int R_, int PAD_, int GS_>
+struct LoopCfg : CfgBase<N_, T_, GS_> {
+  using E = LoopFFT<N_, T_, R_, PAD_>;
+  static constexpr bool kLoop = true;
+  static constexpr int R0 = R_, RL = R_;
+  static constexpr int TWF = E::TW, TWI = 0;
+  static_assert(GS_ >= E::BUF, "group stride too small");
+  __device__ __forceinline__ static int f(int i) { return E::f(i); }
+  __device__ __forceinline__ static void fwd(float2* v, float2* buf, const float2* twf, const float2*, int t) {
+    E::run_fwd(v, buf, twf, t);
+  }
+  __device__ __forceinline__ static void inv(float2* v, float2* buf, const float2* twf, const float2*, int t) {
+    E::run_inv(v, buf, twf, t);
+  }
+  // inverse, mid(v) on natural-order data, forward: one rolled loop
+  template <class Mid>
+  __device__ __forceinline__ static void inv_mid_fwd(float2* v, float2* buf, const float2* twf,
+                                                     const float2*, int t, Mid&& mid) {
+    conj_all(v, E::PTS);
+#pragma unroll 1
+    for (int q = 0; q < 2 * E::NP; ++q) {
+      if (q == E::NP) {
+        conj_all(v, E::PTS);
+        mid(v);
+      }
+      E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t);
+    }
+  }
+  // forward, mid(v) on spectrum-order data, inverse: one rolled loop
+  template <class Mid>
+  __device__ __forceinline__ static void fwd_mid_inv(float2* v, float2* buf, const float2* twf,
+                                                     const float2*, int t, Mid&& mid) {
+#pragma unroll 1
+    for (int q = 0; q < 2 * E::NP; ++q) {
+      if (q == E::NP) {
+        mid(v);
+        conj_all(v, E::PTS);
+      }
+      E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t);
+    }
+    conj_all(v, E::PTS);
+  }
+  static constexpr size_t smem_bytes() {
+    return sizeof(float2) * (size_t)(TWF + TWI + CfgBase<N_, T_, GS_>::NG * GS_);
+  }
+};
+
+template <int N_, int T_, int GS_, class F_, class I_>
+struct GroupCfg : CfgBase<N_, T_, GS_> {
+  using F = F_;
+  using I = I_;
+  static constexpr bool kLoop = false;
+  static constexpr int R0 = F::R0, RL = F::RL;
+  static constexpr int TWF = F::TW, TWI = I::TW;
+  static_assert(GS_ >= F::BUF && GS_ >= I::BUF, "group stride too small");
+  static_assert(F::RL == I::R0 && I::RL == F::R0, "inverse must reverse the radices");
+  __device__ __forceinline__ static int f(int i) { return F::f(i); }
+  __device__ __forceinline__ static void fwd(float2* v, float2* buf, const float2* twf, const float2*, int t) {
+    F::run(v, buf, twf, t);
+  }
+  __device__ __forceinline__ static void inv(float2* v, float2* buf, const float2*, const float2* twi, int t) {
+    I::run(v, buf, twi, t);
+  }
+  template <class Mid>
+  __device__ __forceinline__ static void inv_mid_fwd(float2* v, float2* buf, const float2* twf,
+                                                     const float2* twi, int t, Mid&& mid) {
+    I::run(v, buf, twi, t);
+    mid(v);
+    F::run(v, buf, twf, t);
+  }
+  template <class Mid>
+  __device__ __forceinline__ static void fwd_mid_inv(float2* v, float2* buf, const float2* twf,
+                                                     const float2* twi, int t, Mid&& mid) {
+    F::run(v, buf, twf, t);
+    mid(v);
+    I::run(v, buf, twi, t);
+  }
+  static constexpr size_t smem_bytes() {
+    return sizeof(float2) * (size_t)(TWF + TWI + CfgBase<N_, T_, GS_>::NG * GS_);
+  }
+};
+
+using Rad8x16 = Radices<8, 16>;
+using Rad16x8 = Radices<16, 8>;
+using Rad8x8x3 = Radices<8, 8, 3>;
+using Rad3x8x8 = Radices<3, 8, 8>;
+using Rad8x8x6 = Radices<8, 8, 6>;
+using Rad6x8x8 = Radices<6, 8, 8>;
+
+template <int N>
+struct Cfg;
+template <> struct Cfg<64> : LoopCfg<64, 8, 8, 8, 73> {};
+template <> struct Cfg<128> : GroupCfg<128, 8, 145, GroupFFT<128, 8, 8, -1, Rad8x16>, GroupFFT<128, 8, 16, +1, Rad16x8>> {};
+template <> struct Cfg<192> : GroupCfg<192, 8, 219, GroupFFT<192, 8, 8, -1, Rad8x8x3>, GroupFFT<192, 8, 8, +1, Rad3x8x8>> {};
+template <> struct Cfg<256> : LoopCfg<256, 16, 16, 16, 273> {};
+template <> struct Cfg<384> : GroupCfg<384, 16, 409, GroupFFT<384, 16, 16, -1, Rad8x8x6>, GroupFFT<384, 16, 16, +1, Rad6x8x8>> {};
+template <> struct Cfg<512> : LoopCfg<512, 16, 8, 16, 545> {};
+template <> struct Cfg<1024> : LoopCfg<1024, 32, 32, 32, 1058> {};
+
+// exp(i x) for the phase screen.  For |x| <= pi/4 (|dn| <= 0.38 at the
+// paper's wavelengths and slice thicknesses) the Taylor series of sin and cos
+// truncated after x^11 and x^12 (truncation below 1e-11) is evaluated by
+// Horner's rule in x^2; larger arguments use sincosf.
+__device__ __forceinline__ float2 unit_phasor(float x) {
+  float s, c;
+  if (fabsf(x) <= 0.785398163f) {
+    const float x2 = x * x;
+    const float ps = fmaf(fmaf(fmaf(fmaf(x2, -2.50521084e-8f, 2.75573192e-6f), x2, -1.98412698e-4f), x2,
+                               8.33333333e-3f),
+                          x2, -1.66666667e-1f);
+    s = fmaf(ps, x2 * x, x);
+    c = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(x2, 2.08767570e-9f, -2.75573192e-7f), x2, 2.48015873e-5f), x2,
+                            -1.38888889e-3f),
+                       x2, 4.16666667e-2f),
+                  x2, -0.5f),
+             x2, 1.0f);
+  } else {
+    sincosf(x, &s, &c);
+  }
+  return make_float2(c, s);
+}
+
+// Everything one propagation (or synthesis) launch needs.
+struct StepArgs {
+  float2* work;            // [n][n] working field; holds E_out at the end
+  const float2* ein;       // [n][n] input field (read once)
+  const __half* dn;        // [nz][n][n] index volume (dn = n - n0)
+  float* inten;            // [nz][n][n] or nullptr
+  const float2* ht;        // [n][n] propagator, transposed: ht[kx * n + ky]
+  const float2* tw;        // twiddles: forward table then inverse table
+  float screen_c;          // k0 dz
+  float2 carrier;          // exp(i k0 n0 dz (z_end - z_begin))
+  int z_begin, z_end;
+  // focusing filter (synthesis): multiplier exp(-i kz zf) / (n n) inside the pupil
+  double k0n0, kna2, zf, dx, dy;   // k0 n0, (k0 NA)^2, focal depth, lateral spacings
+  int accumulate;                  // INV_ACC: add into out instead of storing
+  float2* out;                     // INV_ACC destination
+  // team barrier
+  unsigned* bar;
+  int* err;
+  unsigned long long timeout_ns;
+  unsigned bar_extra;
+  // persistent kernel: rows (= columns) per CTA at most, and which per-CTA
+  // buffers live in shared memory (propagator columns, index rows, intensity rows)
+  int rmax;
+  int h_res, dn_stage, i_stage;
+};
+
+// Per-CTA shared-memory copies used by the half-steps (nullptr = use global).
+struct Stage {
+  const float2* h = nullptr;   // propagator columns [col - c0][ky]
+  const __half* dn = nullptr;  // index rows of the current slice [row - r0][x]
+  float* inten = nullptr;      // intensity rows of the current slice [row - r0][x]
+};
+
+// ---------------------------------------------------------------------------
+// memory helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+// --- bulk asynchronous copies (TMA engine, 1D) and mbarriers ---------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* m, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// global -> shared, completion counted on mbarrier m (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src, unsigned bytes, uint64_t* m) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst_smem)),
+      "l"(src), "r"(bytes), "r"(smem_addr(m))
+      : "memory");
+}
+// shared -> global in the calling thread's bulk group
+__device__ __forceinline__ void bulk_store(void* dst, const void* src_smem, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_addr(src_smem)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_reads() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// make this thread's generic-proxy shared-memory writes visible to bulk copies
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bounded wait for an mbarrier phase: gives up after timeout_ns, records
+// kDevErrTimeout and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, unsigned parity, const StepArgs& a) {
+  if (mbar_try_wait(m, parity)) return true;
+  const unsigned long long t0 = global_timer_ns();
+  while (!mbar_try_wait(m, parity)) {
+    if (global_timer_ns() - t0 > a.timeout_ns) {
+      atomicCAS(a.err, 0, kDevErrTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+
+// Team barrier over all CTAs of a cooperative grid.  Arrival is a release
+// add on a counter that the host zeroes before the launch; the wait polls it
+// with acquire loads.  The wait is bounded by timeout_ns (global timer): when
+// it runs out, or another CTA has recorded an error, the CTA records
+// kDevErrTimeout (first error wins) and the caller leaves the kernel.
+__device__ __forceinline__ bool team_barrier(const StepArgs& a, unsigned& epoch, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ++epoch;
+    const unsigned target = epoch * gridDim.x + a.bar_extra;
+    red_release_gpu(a.bar, 1u);
+    int ok = 1;
+    const unsigned long long t0 = global_timer_ns();
+    for (;;) {
+      unsigned v = ld_acquire_gpu(a.bar);
+      if ((int)(v - target) >= 0) break;
+      if (ld_volatile(a.err) != 0) {
+        ok = 0;
+        break;
+      }
+      if (global_timer_ns() - t0 > a.timeout_ns) {
+        atomicCAS(a.err, 0, kDevErrTimeout);
+        ok = 0;
+        break;
+      }
+    }
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// ---------------------------------------------------------------------------
+// half-steps
+// ---------------------------------------------------------------------------
+enum RowMode { ROW_FWD = 0, ROW_STEP = 1, ROW_LAST = 2, ROW_INV_ACC = 3 };
+enum ColMode { COL_PROP = 0, COL_FOCUS = 1 };
+
+template <int N, int T, int R>
+__device__ __forceinline__ void load_layout(float2* v, const float2* __restrict__ src, int t) {
+#pragma unroll
+  for (int k = 0; k < N / T; ++k) v[k] = __ldcg(src + layout_index<N, T, R>(k, t));
+}
+template <int N, int T, int R>
+__device__ __forceinline__ void store_layout(const float2* v, float2* dst, int t) {
+#pragma unroll
+  for (int k = 0; k < N / T; ++k) __stcg(dst + layout_index<N, T, R>(k, t), v[k]);
+}
+
+// Rows [r0, r1) of the team member; each group of T threads takes one row per
+// round.  Groups without a row run the transforms on zeros (so that the warp
+// stays converged for __syncwarp) and skip all memory traffic.
+template <int N, int MODE>
+__device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1, int z, float2* s_buf,
+                                              const float2* s_twf, const float2* s_twi, bool& bad,
+                                              const Stage& st = Stage()) {
+  using C = Cfg<N>;
+  const int lane = threadIdx.x & 31;
+  const int gid = (threadIdx.x >> 5) * C::GPW + lane / C::T;
+  const int t = lane % C::T;
+  float2* buf = s_buf + gid * C::GS;
+  const int rounds = (r1 - r0 + C::NG - 1) / C::NG;
+  for (int k = 0; k < rounds; ++k) {
+    const int row = r0 + k * C::NG + gid;
+    const bool active = row < r1;
+    float2 v[C::PTS];
+    if constexpr (MODE == ROW_FWD) {
+      if (active) load_layout<N, C::T, C::R0>(v, a.ein + (size_t)row * N, t);
+      else
+#pragma unroll
+        for (int q = 0; q < C::PTS; ++q) v[q] = make_float2(0.f, 0.f);
+      C::fwd(v, buf, s_twf, s_twi, t);
+      if (active) store_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
+    } else if constexpr (MODE == ROW_INV_ACC) {
+      if (active) load_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
+      else
+#pragma unroll
+        for (int q = 0; q < C::PTS; ++q) v[q] = make_float2(0.f, 0.f);
+      C::inv(v, buf, s_twf, s_twi, t);
+      if (active) {
+        float2* dst = a.out + (size_t)row * N;
+#pragma unroll
+        for (int q = 0; q < C::PTS; ++q) {
+          const int x = layout_index<N, C::T, C::R0>(q, t);
+          float2 o = v[q];
+          if (a.accumulate) o = cadd(o, __ldcg(dst + x));
+          __stcg(dst + x, o);
+        }
+      }
+    } else {
+      if (active) load_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
+      else
+#pragma unroll
+        for (int q = 0; q < C::PTS; ++q) v[q] = make_float2(0.f, 0.f);
+      // index values: from the shared-memory copy of this CTA's rows when the
+      // slice was prefetched, else fetched from global memory before the
+      // inverse transform so that their latency hides behind it
+      __half dv[C::PTS];
+      if (!st.dn) {
+        const __half* dnrow = a.dn + ((size_t)z * N + (active ? row : r0)) * N;
+#pragma unroll
+        for (int q = 0; q < C::PTS; ++q) dv[q] = __ldcs(dnrow + layout_index<N, C::T, C::R0>(q, t));
+      }
+      const __half* sdn = st.dn ? st.dn + (size_t)((active ? row : r0) - r0) * N : nullptr;
+      float* irow = nullptr;
+      if (active && a.inten)
+        irow = st.inten ? st.inten + (size_t)(row - r0) * N : a.inten + ((size_t)z * N + row) * N;
+      const bool i_smem = st.inten != nullptr;
+      // phase screen exp(i k0 dn dz) and |E|^2 on the natural-order field
+      auto screen = [&](float2* w) {
+#pragma unroll
+        for (int q = 0; q < C::PTS; ++q) {
+          const int x = layout_index<N, C::T, C::R0>(q, t);
+          const float d = __half2float(sdn ? sdn[x] : dv[q]);
+          bad |= active && !isfinite(d);
+          const float2 e = cmul(w[q], unit_phasor(a.screen_c * d));
+          w[q] = e;
+          if (irow) {
+            const float iv = fmaf(e.x, e.x, e.y * e.y);
+            if (i_smem) irow[x] = iv;
+            else __stcs(irow + x, iv);
+          }
+        }
+      };
+      if constexpr (MODE == ROW_LAST) {
+        C::inv(v, buf, s_twf, s_twi, t);
+        screen(v);
+        if (active) {
+#pragma unroll
+          for (int q = 0; q < C::PTS; ++q) v[q] = cmul(v[q], a.carrier);
+          store_layout<N, C::T, C::R0>(v, a.work + (size_t)row * N, t);
+        }
+      } else {
+        C::inv_mid_fwd(v, buf, s_twf, s_twi, t, screen);
+        if (active) store_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
+      }
+    }
+  }
+}
+
+// Columns [c0, c1) of the team member, NG columns per round staged in shared
+// memory (column g of the round at s_buf + g * GS, index padded like the
+// forward transform's exchange buffer).
+template <int N, int MODE>
+__device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1, float2* s_buf,
+                                              const float2* s_twf, const float2* s_twi,
+                                              const Stage& st = Stage()) {
+  using C = Cfg<N>;
+  const int lane = threadIdx.x & 31;
+  const int gid = (threadIdx.x >> 5) * C::GPW + lane / C::T;
+  const int t = lane % C::T;
+  float2* buf = s_buf + gid * C::GS;
+  static_assert(kThreads % C::NG == 0, "");
+  constexpr int YSTEP = kThreads / C::NG;
+  constexpr int PER = N / YSTEP;
+  for (int cb = c0; cb < c1; cb += C::NG) {
+    const int nc = min(C::NG, c1 - cb);
+    __syncthreads();
+    {
+      // each thread keeps one column (cc) and walks y; all loads of a chunk
+      // are issued before any is consumed
+      constexpr int CHUNK = PER % 16 == 0 ? 16 : (PER % 8 == 0 ? 8 : (PER % 4 == 0 ? 4 : 1));
+      static_assert(PER % CHUNK == 0, "");
+      const int cc = threadIdx.x % C::NG, y0 = threadIdx.x / C::NG;
+      const bool on = cc < nc;
+      const float2* src = a.work + cb + cc;
+#pragma unroll
+      for (int c = 0; c < PER; c += CHUNK) {
+        float2 tmp[CHUNK];
+#pragma unroll
+        for (int i = 0; i < CHUNK; ++i)
+          tmp[i] = on ? __ldcg(src + (size_t)(y0 + (c + i) * YSTEP) * N) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < CHUNK; ++i) s_buf[cc * C::GS + C::f(y0 + (c + i) * YSTEP)] = tmp[i];
+      }
+    }
+    __syncthreads();
+    const bool active = gid < nc;
+    const int col = cb + gid;
+    float2 v[C::PTS];
+#pragma unroll
+    for (int q = 0; q < C::PTS; ++q)
+      v[q] = active ? buf[C::f(layout_index<N, C::T, C::R0>(q, t))] : make_float2(0.f, 0.f);
+    __syncwarp();
+    if constexpr (MODE == COL_PROP) {
+      const float2* hcol = st.h ? st.h + (size_t)((active ? col : c0) - c0) * N
+                                : a.ht + (size_t)(active ? col : c0) * N;
+      C::fwd_mid_inv(v, buf, s_twf, s_twi, t, [&](float2* w) {
+#pragma unroll
+        for (int q = 0; q < C::PTS; ++q) {
+          const int ky = layout_index<N, C::T, C::RL>(q, t);
+          w[q] = cmul(w[q], st.h ? hcol[ky] : __ldg(hcol + ky));
+        }
+      });
+    } else {
+      // focusing filter: exp(-i kz zf) / (n n) inside the pupil, 0 outside;
+      // membership decided in FP64 with the same operation order as the oracle
+      const int fx = col < (N + 1) / 2 ? col : col - N;
+      const double kx = __ddiv_rn(__dmul_rn(6.283185307179586, (double)fx), __dmul_rn((double)N, a.dx));
+      const double ndy = __dmul_rn((double)N, a.dy);
+      C::fwd_mid_inv(v, buf, s_twf, s_twi, t, [&](float2* w) {
+#pragma unroll
+        for (int q = 0; q < C::PTS; ++q) {
+          const int ky_i = layout_index<N, C::T, C::RL>(q, t);
+          const int fy = ky_i < (N + 1) / 2 ? ky_i : ky_i - N;
+          const double ky = __ddiv_rn(__dmul_rn(6.283185307179586, (double)fy), ndy);
+          const double kp2 = __dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky));
+          const double kz2 = __dsub_rn(__dmul_rn(a.k0n0, a.k0n0), kp2);
+          float2 m = make_float2(0.f, 0.f);
+          if (kp2 <= a.kna2 && kz2 > 0.0) {
+            double ph = -sqrt(kz2) * a.zf;
+            ph -= 6.283185307179586 * rint(ph * 0.15915494309189535);
+            float sn, cs;
+            sincosf((float)ph, &sn, &cs);
+            const float sc = 1.0f / ((float)N * (float)N);
+            m = make_float2(cs * sc, sn * sc);
+          }
+          w[q] = cmul(w[q], m);
+        }
+      });
+    }
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < C::PTS; ++q) buf[C::f(layout_index<N, C::T, C::R0>(q, t))] = v[q];
+    }
+    __syncthreads();
+    {
+      const int cc = threadIdx.x % C::NG, y0 = threadIdx.x / C::NG;
+      if (cc < nc) {
+        float2* dst = a.work + cb + cc;
+#pragma unroll 8
+        for (int i = 0; i < PER; ++i) {
+          const int y = y0 + i * YSTEP;
+          __stcg(dst + (size_t)y * N, s_buf[cc * C::GS + C::f(y)]);
+        }
+      }
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void load_twiddles(const StepArgs& a, float2* s_twf, float2* s_twi) {
+  using C = Cfg<N>;
+  for (int i = threadIdx.x; i < C::TWF + C::TWI; i += kThreads) {
+    float2 w = __ldg(a.tw + i);
+    if (i < C::TWF) s_twf[i] = w;
+    else s_twi[i - C::TWF] = w;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void report_bad(const StepArgs& a, bool bad) {
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(a.err, 0, kDevErrNan);
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// The whole slice loop in one cooperative launch; gridDim.x CTAs form the team.
+// Shared memory: twiddles | group buffers | [propagator columns of this CTA]
+// | [index rows of the current slice] | [intensity rows of the current slice].
+// The index rows of slice z are fetched by one bulk copy issued when the
+// column half-step of slice z starts, so the HBM read overlaps it; the
+// intensity rows are written to shared memory by the row half-step and sent
+// to HBM by one bulk store that overlaps the next column half-step.
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a) {
+  using C = Cfg<N>;
+  extern __shared__ float4 smem_f4[];
+  float2* s_twf = reinterpret_cast<float2*>(smem_f4);
+  float2* s_twi = s_twf + C::TWF;
+  float2* s_buf = s_twi + C::TWI;
+  char* s_extra = reinterpret_cast<char*>(s_buf + C::NG * C::GS);
+  __shared__ int s_flag;
+  __shared__ __align__(8) uint64_t s_mbar;
+  const int G = gridDim.x, rank = blockIdx.x;
+  const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
+  const int nrow = hi - lo;
+  Stage st;
+  {
+    size_t off = 0;
+    if (a.h_res) {
+      st.h = reinterpret_cast<const float2*>(s_extra + off);
+      off += ((size_t)a.rmax * N * sizeof(float2) + 15) & ~(size_t)15;
+    }
+    if (a.dn_stage) {
+      st.dn = reinterpret_cast<const __half*>(s_extra + off);
+      off += ((size_t)a.rmax * N * sizeof(__half) + 15) & ~(size_t)15;
+    }
+    if (a.i_stage && a.inten) st.inten = reinterpret_cast<float*>(s_extra + off);
+  }
+  if (a.h_res) {
+    float2* dst = const_cast<float2*>(st.h);
+    const float2* src = a.ht + (size_t)lo * N;
+    for (int i = threadIdx.x; i < nrow * N; i += kThreads) dst[i] = __ldg(src + i);
+  }
+  if (threadIdx.x == 0 && a.dn_stage) mbar_init(&s_mbar, 1);
+  load_twiddles<N>(a, s_twf, s_twi);    // ends with __syncthreads
+  unsigned epoch = 0, dn_parity = 0;
+  bool bad = false, dn_pending = false;
+  row_half_step<N, ROW_FWD>(a, lo, hi, a.z_begin, s_buf, s_twf, s_twi, bad);
+  if (!team_barrier(a, epoch, &s_flag)) return;
+  for (int z = a.z_begin; z < a.z_end; ++z) {
+    const bool last = z + 1 == a.z_end;
+    if (a.dn_stage && nrow > 0) {
+      if (threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)((size_t)nrow * N * sizeof(__half));
+        mbar_arrive_expect_tx(&s_mbar, bytes);
+        bulk_load(const_cast<__half*>(st.dn), a.dn + ((size_t)z * N + lo) * N, bytes, &s_mbar);
+      }
+      dn_pending = true;
+    }
+    col_half_step<N, COL_PROP>(a, lo, hi, s_buf, s_twf, s_twi, st);
+    if (!team_barrier(a, epoch, &s_flag)) break;
+    bool ok = true;
+    if (dn_pending) {
+      ok = mbar_wait_bounded(&s_mbar, dn_parity, a);
+      dn_parity ^= 1u;
+      dn_pending = false;
+    }
+    if (st.inten && threadIdx.x == 0) bulk_wait_reads();   // previous intensity store has read its rows
+    if (__syncthreads_or(!ok)) break;
+    if (!last) row_half_step<N, ROW_STEP>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
+    else row_half_step<N, ROW_LAST>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
+    if (st.inten) {
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0 && nrow > 0)
+        bulk_store(a.inten + ((size_t)z * N + lo) * N, st.inten, (unsigned)((size_t)nrow * N * sizeof(float)));
+    }
+    if (!last && !team_barrier(a, epoch, &s_flag)) break;
+  }
+  // leave no copy in flight: a prefetch abandoned by a failed barrier is
+  // waited for (bounded), and every intensity store is completed
+  if (dn_pending) mbar_wait_bounded(&s_mbar, dn_parity, a);
+  if (threadIdx.x == 0) bulk_wait_all();
+  report_bad(a, bad);
+}
+
+// One half-step per launch (comparison path and input synthesis).
+template <int N, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) bpm_row_kernel(StepArgs a, int z) {
+  using C = Cfg<N>;
+  extern __shared__ float4 smem_f4[];
+  float2* s_twf = reinterpret_cast<float2*>(smem_f4);
+  float2* s_twi = s_twf + C::TWF;
+  float2* s_buf = s_twi + C::TWI;
+  load_twiddles<N>(a, s_twf, s_twi);
+  const int G = gridDim.x, rank = blockIdx.x;
+  const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
+  bool bad = false;
+  row_half_step<N, MODE>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+  if constexpr (MODE == ROW_STEP || MODE == ROW_LAST) report_bad(a, bad);
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) bpm_col_kernel(StepArgs a) {
+  using C = Cfg<N>;
+  extern __shared__ float4 smem_f4[];
+  float2* s_twf = reinterpret_cast<float2*>(smem_f4);
+  float2* s_twi = s_twf + C::TWF;
+  float2* s_buf = s_twi + C::TWI;
+  load_twiddles<N>(a, s_twf, s_twi);
+  const int G = gridDim.x, rank = blockIdx.x;
+  const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
+  col_half_step<N, MODE>(a, lo, hi, s_buf, s_twf, s_twi);
+}
+
+// Light sheet: the ky = 0 spectrum line, inverse FFT_x by group 0 of warp 0,
+// then the row is copied to every y.  Every CTA computes the (short) line
+// itself and writes a share of the rows.  Dynamic shared memory: smem_bytes()
+// plus GS float2 for the spectrum line.
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) bpm_light_sheet_kernel(StepArgs a, double w0, double xc) {
+  using C = Cfg<N>;
+  extern __shared__ float4 smem_f4[];
+  float2* s_twf = reinterpret_cast<float2*>(smem_f4);
+  float2* s_twi = s_twf + C::TWF;
+  float2* s_buf = s_twi + C::TWI;
+  float2* line = s_buf + C::NG * C::GS;
+  __shared__ double s_part[kThreads];
+  load_twiddles<N>(a, s_twf, s_twi);
+  const double nd = __dmul_rn((double)N, a.dx);
+  // sum of A(kx) over propagating bins (FP64)
+  double part = 0.0;
+  for (int x = threadIdx.x; x < N; x += kThreads) {
+    const int f = x < (N + 1) / 2 ? x : x - N;
+    const double kx = __ddiv_rn(__dmul_rn(6.283185307179586, (double)f), nd);
+    const double kz2 = __dsub_rn(__dmul_rn(a.k0n0, a.k0n0), __dmul_rn(kx, kx));
+    if (kz2 > 0.0) {
+      const double u = kx * w0 * 0.5;
+      part += exp(-u * u);
+    }
+  }
+  s_part[threadIdx.x] = part;
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) s_part[threadIdx.x] += s_part[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double sumA = s_part[0];
+  for (int x = threadIdx.x; x < N; x += kThreads) {
+    const int f = x < (N + 1) / 2 ? x : x - N;
+    const double kx = __ddiv_rn(__dmul_rn(6.283185307179586, (double)f), nd);
+    const double kz2 = __dsub_rn(__dmul_rn(a.k0n0, a.k0n0), __dmul_rn(kx, kx));
+    float2 sv = make_float2(0.f, 0.f);
+    if (kz2 > 0.0) {
+      const double u = kx * w0 * 0.5;
+      const double amp = exp(-u * u) / sumA;
+      double ph = -(kx * xc) - sqrt(kz2) * a.zf;
+      ph -= 6.283185307179586 * rint(ph * 0.15915494309189535);
+      double sn, cs;
+      sincos(ph, &sn, &cs);
+      sv = make_float2((float)(amp * cs), (float)(amp * sn));
+    }
+    line[C::f(x)] = sv;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int t = threadIdx.x % C::T;
+    const int g = threadIdx.x / C::T;
+    float2 v[C::PTS];
+#pragma unroll
+    for (int q = 0; q < C::PTS; ++q) v[q] = line[C::f(layout_index<N, C::T, C::RL>(q, t))];
+    __syncwarp();
+    C::inv(v, s_buf + g * C::GS, s_twf, s_twi, t);
+    if (g == 0) {
+#pragma unroll
+      for (int q = 0; q < C::PTS; ++q) line[C::f(layout_index<N, C::T, C::R0>(q, t))] = v[q];
+    }
+  }
+  __syncthreads();
+  for (size_t i = blockIdx.x * (size_t)kThreads + threadIdx.x; i < (size_t)N * N;
+       i += (size_t)gridDim.x * kThreads) {
+    const int x = (int)(i % N);
+    __stcg(a.work + i, line[C::f(x)]);
+  }
+}
+
+// Scatter emitters: out[iy][ix] += amp exp(i phase).  One thread per emitter.
+__global__ void bpm_scatter_kernel(float2* field, int n, const int* idx, const double* phase, int count,
+                                   const unsigned long long* n_pupil) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= count) return;
+  const double np = (double)*n_pupil;
+  if (np <= 0.0) return;
+  const double amp = sqrt((double)n * (double)n / np);
+  double sn, cs;
+  sincos(phase[j], &sn, &cs);
+  float* p = reinterpret_cast<float*>(field + idx[j]);
+  atomicAdd(p, (float)(amp * cs));
+  atomicAdd(p + 1, (float)(amp * sn));
+}
+
+// Count DFT bins inside the pupil |k_perp|^2 <= kna2 that also propagate.
+__global__ void bpm_pupil_count_kernel(int n, double dx, double dy, double k0n0, double kna2,
+                                       unsigned long long* count) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  unsigned long long c = 0;
+  if (i < (size_t)n * n) {
+    const int x = (int)(i % n), y = (int)(i / n);
+    const int fx = x < (n + 1) / 2 ? x : x - n, fy = y < (n + 1) / 2 ? y : y - n;
+    const double kx = __ddiv_rn(__dmul_rn(6.283185307179586, (double)fx), __dmul_rn((double)n, dx));
+    const double ky = __ddiv_rn(__dmul_rn(6.283185307179586, (double)fy), __dmul_rn((double)n, dy));
+    const double kp2 = __dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky));
+    const double kz2 = __dsub_rn(__dmul_rn(k0n0, k0n0), kp2);
+    c = (kp2 <= kna2 && kz2 > 0.0) ? 1ull : 0ull;
+  }
+  // warp reduce, one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// Propagator table, transposed: ht[kx * ny + ky] = exp(i (kz - k0 n0) dz) / (nx ny)
+// for kz^2 = (k0 n0)^2 - kx^2 - ky^2 > 0, else 0.  FP64 throughout; the
+// cancellation-free form kz - k0 n0 = -k_perp^2 / (k0 n0 + kz) is used.
+__global__ void bpm_build_ht_kernel(float2* ht, int nx, int ny, double dx, double dy, double dz, double lambda,
+                                    double n0) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)nx * ny) return;
+  const int kyi = (int)(i % ny), kxi = (int)(i / ny);
+  const int fx = kxi < (nx + 1) / 2 ? kxi : kxi - nx;
+  const int fy = kyi < (ny + 1) / 2 ? kyi : kyi - ny;
+  const double twopi = 6.283185307179586;
+  const double K = __dmul_rn(__ddiv_rn(twopi, lambda), n0);
+  const double kx = __ddiv_rn(__dmul_rn(twopi, (double)fx), __dmul_rn((double)nx, dx));
+  const double ky = __ddiv_rn(__dmul_rn(twopi, (double)fy), __dmul_rn((double)ny, dy));
+  const double kz2 = __dsub_rn(__dsub_rn(__dmul_rn(K, K), __dmul_rn(kx, kx)), __dmul_rn(ky, ky));
+  float2 h = make_float2(0.f, 0.f);
+  if (kz2 > 0.0) {
+    const double kp2 = kx * kx + ky * ky;
+    const double ph = -kp2 / (K + sqrt(kz2)) * dz;
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    const double sc = 1.0 / ((double)nx * (double)ny);
+    h = make_float2((float)(cs * sc), (float)(sn * sc));
+  }
+  ht[i] = h;
+}
+
+}  // namespace bpmk
