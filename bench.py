@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the split-step beam-propagation hot path on B300.
+
+Workload (the paper's headline case, Biobeam arXiv:1706.02261 method
+paragraph: a ~1000-PSF multiplexed field through 1024^3 voxels): a
+1024 x 1024 x 1024 grid, dx = dz = 0.1625 um, lambda = 0.5 um, n0 = 1.33, a
+seeded 800-sphere FP16 tissue phantom, and an input field of 32 x 32 focused
+emitters (NA 0.6, random phases, one seeded focal depth).  Inputs are synthetic
+(paper_1706_02261_b300.inputs); the paper uses no public dataset.
+
+One step = the multiplexed input synthesis (bpm_multiplex_psf) plus the
+propagation through all 1024 slices with the FP32 intensity volume written
+(bpm_propagate).  The plan (propagator table, twiddles) is built once outside
+the timed region, as a user reuses it for every field.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank propagates its own
+replica of the workload on its own GPU (the path has no data exchange between
+fields); the elapsed time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxel-steps/s (1024^3 multiplexed-PSF propagation)"
+UNIT = "voxel-steps/s"
+PAPER_VOXEL_STEPS_PER_S = 1024 ** 3 / 0.5     # "< 500 ms" per 1024^3 field (context)
+FP32_LANES_PER_SM = 128
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nz", type=int, default=1024, help="slices (default: the full 1024)")
+    ap.add_argument("--cpu-slices", type=int, default=2, help="slices in the oracle's timed sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def step_flops(n: int, nz: int) -> float:
+    """Algorithmic FLOPs of one propagation: per slice a forward and an inverse
+    2D FFT credited 5 M log2 M each, the propagator and screen complex
+    multiplies (6 M each) and |E|^2 (3 M)."""
+    M = n * n
+    return nz * (10.0 * M * math.log2(M) + 15.0 * M)
+
+
+def step_bytes(n: int, nz: int) -> float:
+    """Algorithmic HBM bytes of one propagation: FP16 index and FP32 intensity
+    per voxel, plus the input and output fields."""
+    M = n * n
+    return nz * M * (2 + 4) + 2 * M * 8
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def make_workload(nz: int):
+    from paper_1706_02261_b300 import inputs
+    w = inputs.multiplex_1024(nz=nz)
+    dn = w.dn()
+    return w, dn, w.foci()
+
+
+def cpu_baseline(w, dn16, foci, slices: int):
+    """The FP64 oracle, as it stands, on the first ``slices`` slices of the
+    same workload (synthesis of the same multiplexed field + propagation)."""
+    import oracle
+    from paper_1706_02261_b300 import inputs
+    dn64 = inputs.dn_to_f64(dn16[:slices])
+    t0 = time.perf_counter()
+    E0 = oracle.multiplex_psf(w.n, w.n, w.d, w.d, w.lam, w.n0, foci.ix, foci.iy, foci.phase, foci.zf, foci.NA)
+    oracle.bpm(dn64, E0, w.d, w.d, w.d, w.lam, w.n0)
+    dt = time.perf_counter() - t0
+    return {"value": w.n * w.n * slices / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{w.n}x{w.n}x{slices} slices of the 1024^3 workload incl. the multiplexed synthesis "
+                      f"({dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w, dn16, foci = make_workload(args.nz)
+    k = args.cpu_slices
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_baseline(w, dn16, foci, 1)
+    times = []
+    cores = 1
+    for _ in range(args.steps):
+        r = cpu_baseline(w, dn16, foci, k)
+        cores = r["cores"]
+        times.append(w.n * w.n * k / r["value"])
+    t = statistics.mean(times)
+    value = w.n * w.n * k / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"multiplex1024: {w.n}x{w.n}x{k}-slice sample per step of the 1024^3 "
+                                   f"multiplexed-PSF workload (FP64 CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{k} slices of 1024x1024 per step, with the multiplexed synthesis"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("bpm.cu", "bpm_kernels.cuh", "fft.cuh"):
+        with open(os.path.join(ROOT, "paper_1706_02261_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the CUDA library is the only compute path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=dev)
+    from paper_1706_02261_b300 import build as build_mod
+    build_mod.build()
+    from paper_1706_02261_b300 import bpm as B
+
+    w, dn16, foci = make_workload(args.nz)
+    n, nz = w.n, w.nz
+    xyz = foci.xyz_um(w.d, w.d)
+    stream = torch.cuda.current_stream(dev)
+
+    t0 = time.perf_counter()
+    plan = B.bpm_plan(B.Instance(n, nz, w.d, w.d, w.lam, w.n0))
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    info = B.bpm_plan_info(plan)
+    dn_d = torch.from_numpy(dn16).to(dev)
+    e0 = torch.empty((n, n), dtype=torch.complex64, device=dev)
+    eout = torch.empty_like(e0)
+    inten = torch.empty((nz, n, n), dtype=torch.float32, device=dev)
+
+    kev = []
+
+    def step(record=False):
+        B.bpm_multiplex_psf(plan, 0, xyz, foci.phase, foci.NA, e0, stream)
+        if record:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            B.bpm_propagate(plan, dn_d, e0, eout, inten, 0, nz, stream)
+            b.record(stream)
+            kev.append((a, b))
+        else:
+            B.bpm_propagate(plan, dn_d, e0, eout, inten, 0, nz, stream)
+
+    for _ in range(args.warmup):
+        step()
+    if B.bpm_check(plan) != 0:
+        raise SystemExit(f"device error during warm-up: {B.bpm_last_error()}")
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    with ClockSampler(local) as clocks:
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+        ev1.record(stream)
+        barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if B.bpm_check(plan) != 0:
+        raise SystemExit(f"device error in the timed region: {B.bpm_last_error()}")
+    kern_s = statistics.mean(a.elapsed_time(b) for a, b in kev) / 1e3
+    if ws > 1:
+        t = torch.tensor([elapsed, kern_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed, kern_s = float(t[0]), float(t[1])
+    vox = float(n) * n * nz
+    value = vox * args.steps * ws / elapsed
+
+    # end to end through the C ABI with host buffers: every step copies its
+    # index volume host->device and its intensity volume and output field
+    # device->host (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        dn_h = torch.from_numpy(dn16).pin_memory()
+        i_h = torch.empty((nz, n, n), dtype=torch.float32).pin_memory()
+        e_h = torch.empty((n, n), dtype=torch.complex64).pin_memory()
+        dn_d.copy_(dn_h, non_blocking=True)
+        step()
+        i_h.copy_(inten, non_blocking=True)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            dn_d.copy_(dn_h, non_blocking=True)
+            step()
+            i_h.copy_(inten, non_blocking=True)
+            e_h.copy_(eout, non_blocking=True)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t[0])
+        e2e = {"value": vox * args.steps * ws / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(dn_h.numel() * dn_h.element_size() + xyz.nbytes + foci.phase.nbytes),
+               "d2h_bytes_per_step": int(i_h.numel() * 4 + e_h.numel() * 8)}
+
+    peaks, peak_src = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    props = torch.cuda.get_device_properties(dev)
+    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = step_flops(n, nz) / kern_s / 1e12
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "persistent1024_traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            tj = json.load(f)
+        if tj.get("kernel_source_hash") == _kernel_hash():
+            traffic = tj.get("bytes_per_full_launch")
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": traffic,
+                "peak_source": f"derived: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                               f"x {sm_max:.0f} MHz ({peak_src} max SM clock)",
+                "kernel": "bpm_persistent_kernel<1024>", "kernel_ms": kern_s * 1e3,
+                "algorithmic_flops": step_flops(n, nz), "algorithmic_bytes": step_bytes(n, nz),
+                "hbm_achieved_gbs": step_bytes(n, nz) / kern_s / 1e9, "hbm_peak_gbs": hbm_peak,
+                "hbm_frac_of_measured": step_bytes(n, nz) / kern_s / 1e9 / hbm_peak}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(w, dn16, foci, args.cpu_slices)
+
+    launches_per_step = 6     # pupil count, scatter, 3 synthesis half-steps, persistent propagation
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": value / (PAPER_VOXEL_STEPS_PER_S * ws), "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"multiplex1024: {n}x{n}x{nz} voxels, dx=dz={w.d} um, lambda={w.lam} um, "
+                                   f"n0={w.n0}, 800-sphere FP16 phantom (seed 2), 32x32 foci NA 0.6",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (2 GiB index volume, 4 GiB intensity volume per step)",
+                       "team_ctas": info["team_ctas"], "plan_ms": plan_ms},
+            "roofline": roofline, "clocks": clocks.summary(), "gpu_launches": launches_per_step * args.steps,
+            "e2e": e2e, "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    B.bpm_free(plan)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
