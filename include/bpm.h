@@ -104,6 +104,35 @@ int bpm_propagate(bpm_plan_t p, const void *const *d_dn, const void *const *d_Ei
                   void *const *d_Eout, float *const *d_I, int z_begin, int z_end,
                   cudaStream_t stream);
 
+/* bpm_propagate_static - the same propagation as bpm_propagate for one
+ * instance, for callers that cannot allocate device memory.  Some callers run
+ * inside a host application whose allocator owns the whole device (cudaMalloc
+ * would fail or break its accounting), or in a loop where the device-wide
+ * synchronisation of cudaMalloc/cudaFree is not acceptable, or must not risk
+ * an out-of-memory failure after start-up.  This entry point allocates nothing
+ * and needs no plan: the propagator table, the twiddle tables, the barrier
+ * counter and the error word live in one fixed array of device memory inside
+ * the library (about 528 KiB), which every GPU that loads the library keeps
+ * until the process exits.  The paper has no counterpart; it is a service of
+ * this library.
+ *   inst          : one problem description; nx = ny must be 64, 128, 192 or
+ *                   256 (larger grids return BPM_ERR_UNSUPPORTED: the fixed
+ *                   array holds the propagator of a 256 x 256 grid at most)
+ *   d_dn, d_Ein, d_Eout, d_I, z_begin, z_end : as for bpm_propagate, for this
+ *                   one instance (d_I may be NULL)
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call rebuilds the tables and clears the counter
+ * and error word on `stream`, runs the propagation, then synchronises `stream`
+ * and returns the device status (BPM_ERR_TIMEOUT, BPM_ERR_NAN) directly.  All
+ * calls on a device share the array, so calls that overlap on the GPU (other
+ * streams, other host threads) race and give wrong results; issue them one at
+ * a time.
+ * Errors: BPM_ERR_ARG, BPM_ERR_ALIGN, BPM_ERR_UNSUPPORTED, BPM_ERR_CUDA,
+ * BPM_ERR_TIMEOUT, BPM_ERR_NAN. */
+int bpm_propagate_static(const bpm_instance_desc *inst, const void *d_dn, const void *d_Ein,
+                         void *d_Eout, float *d_I, int z_begin, int z_end, cudaStream_t stream);
+
 /* bpm_multiplex_psf - the multiplexed input field of the method paragraph:
  * the sum of n_foci focused fields, one per emitter.  Emitter j sits at the
  * grid point nearest to (h_xyz[3j], h_xyz[3j+1]) (rounded in FP64 as

@@ -60,8 +60,9 @@ _lib.bpm_free.argtypes = [_vp]
 _lib.bpm_last_error.restype = ctypes.c_char_p
 _lib.bpm_plan_info.argtypes = [_vp, ctypes.POINTER(_i), _i]
 _lib.bpm_debug_set_barrier_timeout.argtypes = [_vp, ctypes.c_ulonglong, _u]
+_lib.bpm_propagate_static.argtypes = [ctypes.POINTER(bpm_instance_desc), _vp, _vp, _vp, _vp, _i, _i, _vp]
 for _f in ("bpm_plan", "bpm_propagate", "bpm_multiplex_psf", "bpm_light_sheet", "bpm_check",
-           "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout"):
+           "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout", "bpm_propagate_static"):
     getattr(_lib, _f).restype = _i
 
 
@@ -175,3 +176,12 @@ def bpm_plan_info(plan) -> dict:
 
 def bpm_debug_set_barrier_timeout(plan, timeout_ns: int, extra_arrivals: int = 0) -> int:
     return _check(_lib.bpm_debug_set_barrier_timeout(plan, timeout_ns, extra_arrivals))
+
+
+def bpm_propagate_static(instance: "Instance", dn, e_in, e_out, inten=None, z_begin: int = 0,
+                         z_end: int = 2 ** 31 - 1, stream=None) -> int:
+    """Allocation-free propagation of one instance (grids up to 256 x 256);
+    synchronises the stream and returns the device status."""
+    desc = instance.desc()
+    return _check(_lib.bpm_propagate_static(ctypes.byref(desc), _ptr(dn), _ptr(e_in), _ptr(e_out),
+                                            _ptr(inten), z_begin, z_end, _stream_handle(stream)))

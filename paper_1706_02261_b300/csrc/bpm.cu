@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -550,4 +551,207 @@ extern "C" int bpm_debug_set_barrier_timeout(bpm_plan_t p, unsigned long long ti
   p->timeout_ns = timeout_ns;
   p->bar_extra = extra;
   return BPM_OK;
+}
+
+// ---- allocation-free propagation ----------------------------------------------
+//
+// For callers that must not allocate device memory (see bpm_propagate_static in
+// bpm.h): everything the persistent kernel needs besides the caller's buffers
+// lives in one file-scope device array.  Layout: [0, 256) barrier counter
+// (offset 0) and error word (offset 64); then the twiddle tables; then the
+// transposed propagator table for the largest supported grid.
+namespace {
+
+constexpr int kStaticMaxN = 256;
+constexpr size_t kStaticWordsBytes = 256;
+constexpr size_t kStaticTwiddleFloat2 = 2048;
+constexpr size_t kStaticTwiddleBytes = kStaticTwiddleFloat2 * sizeof(float2);
+constexpr size_t kStaticPropBytes = (size_t)kStaticMaxN * kStaticMaxN * sizeof(float2);
+constexpr size_t kStaticScratchBytes = kStaticWordsBytes + kStaticTwiddleBytes + kStaticPropBytes;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char bpm_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mutex;
+unsigned char* g_static_ptr[kStaticMaxDevices] = {};
+
+// Radix schedule of one transform, passed by value to the twiddle kernel.
+struct TwSchedule {
+  int n, t, count, sign;
+  int r[4];
+};
+
+// Same table as append_twiddles(), built on the device in FP64: entry
+// (b R + r) T + t of pass p >= 1 holds W_{Ns R}^{(j mod Ns) r}, j = t + b T.
+__global__ void bpm_static_twiddle_kernel(float2* out, TwSchedule s) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (s.count - 1) * s.n) return;
+  const int p = 1 + e / s.n, local = e % s.n;
+  int Ns = 1;
+  for (int i = 0; i < p; ++i) Ns *= s.r[i];
+  const int R = s.r[p];
+  const int t = local % s.t, br = local / s.t;
+  const int r = br % R, b = br / R;
+  const int j = t + b * s.t;
+  const long long ex = (long long)(j % Ns) * r % (long long)(Ns * R);
+  const double ang = s.sign * 6.283185307179586 * (double)ex / (double)(Ns * R);
+  double sn, cs;
+  sincos(ang, &sn, &cs);
+  out[e] = make_float2((float)cs, (float)sn);
+}
+
+template <class RS>
+TwSchedule schedule_of(int n, int t, int sign) {
+  TwSchedule s{};
+  s.n = n;
+  s.t = t;
+  s.count = RS::count;
+  s.sign = sign;
+  for (int i = 0; i < RS::count && i < 4; ++i) s.r[i] = RS::at(i);
+  return s;
+}
+
+int launch_static_twiddles(const TwSchedule& s, float2* dst, cudaStream_t stream) {
+  const int total = (s.count - 1) * s.n;
+  if (total <= 0) return BPM_OK;
+  bpm_static_twiddle_kernel<<<(total + 255) / 256, 256, 0, stream>>>(dst, s);
+  BPM_CU(cudaGetLastError());
+  return BPM_OK;
+}
+
+template <int N>
+int static_propagate(const bpm_instance_desc& d, unsigned char* scratch, const void* d_dn, const void* d_Ein,
+                     void* d_Eout, float* d_I, int zb, int ze, cudaStream_t stream) {
+  using C = Cfg<N>;
+  static_assert(C::TWF + C::TWI <= (int)kStaticTwiddleFloat2, "twiddle region too small");
+  // launch configuration: the same rule as a plan's (setup_kernels)
+  int sms = 0, dev = 0, max_optin = 0;
+  BPM_CU(cudaGetDevice(&dev));
+  BPM_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  BPM_CU(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  NRes r;
+  r.n = N;
+  r.smem = C::smem_bytes();
+  r.team = std::max(1, std::min((N + C::NG - 1) / C::NG, sms));
+  r.rmax = (N + r.team - 1) / r.team;
+  auto rup = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  const size_t hb = rup((size_t)r.rmax * N * sizeof(float2)), db = rup((size_t)r.rmax * N * 2),
+               ib = rup((size_t)r.rmax * N * sizeof(float));
+  const size_t budget = (size_t)max_optin - 1024;
+  r.h_res = r.dn_stage = r.i_stage = 1;
+  if (r.smem + hb + db + ib > budget) r.h_res = 0;
+  if (r.smem + db + ib > budget) r.i_stage = 0;
+  if (r.smem + db > budget) r.dn_stage = 0;
+  r.smem_persist = r.smem + (r.h_res ? hb : 0) + (r.dn_stage ? db : 0) + (r.i_stage ? ib : 0);
+  BPM_CU(cudaFuncSetAttribute(bpm_persistent_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)r.smem_persist));
+  unsigned* bar = reinterpret_cast<unsigned*>(scratch);
+  int* err = reinterpret_cast<int*>(scratch + 64);
+  float2* tw = reinterpret_cast<float2*>(scratch + kStaticWordsBytes);
+  float2* ht = reinterpret_cast<float2*>(scratch + kStaticWordsBytes + kStaticTwiddleBytes);
+  // the array keeps the previous call's contents: clear the barrier counter
+  // and the error word, rebuild both tables
+  BPM_CU(cudaMemsetAsync(scratch, 0, kStaticWordsBytes, stream));
+  int rc;
+  if constexpr (C::kLoop) {
+    TwSchedule s{};
+    s.n = N;
+    s.t = C::T;
+    s.count = C::E::NP;
+    s.sign = -1;
+    for (int i = 0; i < C::E::NP && i < 4; ++i) s.r[i] = C::E::R;
+    rc = launch_static_twiddles(s, tw, stream);
+  } else {
+    rc = launch_static_twiddles(schedule_of<typename C::F::Rad>(N, C::T, -1), tw, stream);
+    if (rc == BPM_OK) rc = launch_static_twiddles(schedule_of<typename C::I::Rad>(N, C::T, +1), tw + C::TWF, stream);
+  }
+  if (rc) return rc;
+  const size_t M = (size_t)N * N;
+  bpm_build_ht_kernel<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>(ht, d.nx, d.ny, d.dx, d.dy, d.dz, d.lambda,
+                                                                       d.n0);
+  BPM_CU(cudaGetLastError());
+  StepArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.ht = ht;
+  a.tw = tw;
+  const double k0 = kTwoPi / d.lambda;
+  a.screen_c = (float)(k0 * d.dz);
+  a.k0n0 = k0 * d.n0;
+  a.dx = d.dx;
+  a.dy = d.dy;
+  a.bar = bar;
+  a.err = err;
+  a.timeout_ns = 2000000000ull;
+  a.rmax = r.rmax;
+  a.h_res = r.h_res;
+  a.dn_stage = r.dn_stage;
+  a.i_stage = r.i_stage;
+  a.work = static_cast<float2*>(d_Eout);
+  a.ein = static_cast<const float2*>(d_Ein);
+  a.dn = static_cast<const __half*>(d_dn);
+  a.inten = d_I;
+  a.z_begin = zb;
+  a.z_end = ze;
+  const double ph = std::fmod(k0 * d.n0 * d.dz * (double)(ze - zb), kTwoPi);
+  a.carrier = make_float2((float)std::cos(ph), (float)std::sin(ph));
+  void* args[] = {&a};
+  BPM_CU(cudaLaunchCooperativeKernel((const void*)bpm_persistent_kernel<N>, dim3(r.team), dim3(kThreads), args,
+                                     r.smem_persist, stream));
+  BPM_CU(cudaStreamSynchronize(stream));
+  int e = 0;
+  BPM_CU(cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e == BPM_ERR_TIMEOUT) return fail(BPM_ERR_TIMEOUT, "a device barrier wait ran out of time");
+  if (e == BPM_ERR_NAN) return fail(BPM_ERR_NAN, "non-finite value in the refractive-index volume");
+  if (e != 0) return fail(e, "device error %d", e);
+  return BPM_OK;
+}
+
+}  // namespace
+
+extern "C" int bpm_propagate_static(const bpm_instance_desc* inst, const void* d_dn, const void* d_Ein,
+                                    void* d_Eout, float* d_I, int z_begin, int z_end, cudaStream_t stream) {
+  if (!inst) return fail(BPM_ERR_ARG, "inst is NULL");
+  int rc = check_desc(*inst, 0);
+  if (rc) return rc;
+  if (inst->nx > kStaticMaxN)
+    return fail(BPM_ERR_UNSUPPORTED,
+                "bpm_propagate_static handles grids up to %d x %d (its fixed device scratch is %zu bytes); "
+                "got %d x %d, use bpm_plan/bpm_propagate", kStaticMaxN, kStaticMaxN, kStaticScratchBytes,
+                inst->nx, inst->ny);
+  if (z_begin < 0 || z_end < z_begin) return fail(BPM_ERR_ARG, "need 0 <= z_begin <= z_end");
+  const int zb = std::min(z_begin, inst->nz), ze = std::min(z_end, inst->nz);
+  if (!d_Ein || !d_Eout || (ze > zb && !d_dn)) return fail(BPM_ERR_ARG, "NULL device pointer");
+  if (!aligned16(d_Ein) || !aligned16(d_Eout) || !aligned16(d_dn) || !aligned16(d_I))
+    return fail(BPM_ERR_ALIGN, "device pointers must be 16-byte aligned");
+  int dev = 0;
+  BPM_CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(BPM_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+  unsigned char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+      void* p = nullptr;
+      BPM_CU(cudaGetSymbolAddress(&p, bpm_static_scratch));
+      g_static_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    scratch = g_static_ptr[dev];
+  }
+  if (ze == zb) {
+    if (d_Eout != d_Ein)
+      BPM_CU(cudaMemcpyAsync(d_Eout, d_Ein, (size_t)inst->nx * inst->ny * sizeof(float2), cudaMemcpyDeviceToDevice,
+                             stream));
+    BPM_CU(cudaStreamSynchronize(stream));
+    return BPM_OK;
+  }
+  switch (inst->nx) {
+    case 64: return static_propagate<64>(*inst, scratch, d_dn, d_Ein, d_Eout, d_I, zb, ze, stream);
+    case 128: return static_propagate<128>(*inst, scratch, d_dn, d_Ein, d_Eout, d_I, zb, ze, stream);
+    case 192: return static_propagate<192>(*inst, scratch, d_dn, d_Ein, d_Eout, d_I, zb, ze, stream);
+    case 256: return static_propagate<256>(*inst, scratch, d_dn, d_Ein, d_Eout, d_I, zb, ze, stream);
+  }
+  return fail(BPM_ERR_UNSUPPORTED, "grid size %d is not supported", inst->nx);
 }
