@@ -1,7 +1,8 @@
 // fft.cuh - register/shared-memory FFT building blocks for sm_103a.
 //
-// One 1D transform of length N is computed by a group of T threads (T <= 32,
-// so a group never spans warps and only __syncwarp is needed).  Each thread
+// One 1D transform of length N is computed by a group of T threads (a part of
+// one warp, synchronised by __syncwarp, or whole warps, synchronised by a
+// named barrier of the group).  Each thread
 // keeps N/T points in registers.  The transform is a mixed-radix Stockham
 // decomposition N = R_0 R_1 ... R_{P-1}: pass p performs N/R_p radix-R_p
 // butterflies (B = N/(R_p T) per thread) fully in registers, and the passes
@@ -100,6 +101,18 @@ __device__ __forceinline__ float2 twc(float2 a) {
     constexpr float c = (float)ct_cos(ct_angle(e, R));
     constexpr float s = (float)(S * ct_sin(ct_angle(e, R)));
     return cmul(a, make_float2(c, s));
+  }
+}
+
+// Synchronise the T threads of one transform group: a warp-level barrier
+// when the group sits inside one warp, else the named CTA barrier bar_id
+// (1..15) over the group's T threads (T a multiple of 32).
+template <int T>
+__device__ __forceinline__ void group_sync(int bar_id) {
+  if constexpr (T <= 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "n"(T) : "memory");
   }
 }
 
@@ -216,12 +229,12 @@ struct GroupFFT {
   static constexpr int BUF = N + N / PAD;          // exchange buffer length (float2)
   static constexpr int TW = (NP - 1) * N;          // twiddle table length (float2)
   static_assert(RS::product() == N, "radices must multiply to N");
-  static_assert(T <= 32 && 32 % T == 0, "a group must sit inside one warp");
+  static_assert((T <= 32 && 32 % T == 0) || T % 32 == 0, "a group is part of one warp or whole warps");
 
   __device__ __forceinline__ static int f(int i) { return i + i / PAD; }
 
   template <int p>
-  __device__ __forceinline__ static void pass(float2* v, float2* buf, const float2* tw, int t) {
+  __device__ __forceinline__ static void pass(float2* v, float2* buf, const float2* tw, int t, int bar_id) {
     constexpr int R = RS::at(p);
     constexpr int B = N / (R * T);
     constexpr int Ns = RS::prefix(p);
@@ -244,7 +257,7 @@ struct GroupFFT {
 #pragma unroll
         for (int r = 0; r < R; ++r) buf[f(base + r * Ns)] = v[b * R + r];
       }
-      __syncwarp();
+      group_sync<T>(bar_id);
       constexpr int Rn = RS::at(p + 1);
       constexpr int Bn = N / (Rn * T);
 #pragma unroll
@@ -253,15 +266,16 @@ struct GroupFFT {
 #pragma unroll
         for (int r = 0; r < Rn; ++r) v[b * Rn + r] = buf[f(j + r * (N / Rn))];
       }
-      __syncwarp();
-      pass<p + 1>(v, buf, tw, t);
+      group_sync<T>(bar_id);
+      pass<p + 1>(v, buf, tw, t, bar_id);
     }
   }
 
   // v: L(R0) in, L(RL) out.  buf: this group's BUF-long exchange buffer.
   // tw: this transform's twiddle table (TW entries, may be in shared memory).
-  __device__ __forceinline__ static void run(float2* v, float2* buf, const float2* tw, int t) {
-    pass<0>(v, buf, tw, t);
+  // bar_id: named barrier of the group when T > 32 (unused otherwise).
+  __device__ __forceinline__ static void run(float2* v, float2* buf, const float2* tw, int t, int bar_id = 0) {
+    pass<0>(v, buf, tw, t, bar_id);
   }
 };
 
@@ -297,6 +311,7 @@ __device__ __forceinline__ void conj_all(float2* v, int n) {
 template <int N_, int T_, int R_, int PAD_>
 struct LoopFFT {
   static constexpr int N = N_, T = T_, R = R_, PAD = PAD_;
+  static constexpr int R0 = R_, RL = R_;
   static constexpr int NP = ilog_ceil(N_, R_);
   static constexpr int LGR = ilog2_ceil(R_);
   static constexpr int PTS = N / T;
@@ -305,12 +320,13 @@ struct LoopFFT {
   static constexpr int TW = (NP - 1) * N;
   static_assert((1 << LGR) == R, "radix must be a power of two");
   static_assert(B * R * T == N && B >= 1, "each thread must own whole butterflies");
-  static_assert(T <= 32 && 32 % T == 0, "a group must sit inside one warp");
+  static_assert((T <= 32 && 32 % T == 0) || T % 32 == 0, "a group is part of one warp or whole warps");
 
   __device__ __forceinline__ static int f(int i) { return i + i / PAD; }
 
   // forward Stockham pass p; registers L(R) in and out
-  __device__ __forceinline__ static void pass(int p, float2* v, float2* buf, const float2* tw, int t) {
+  __device__ __forceinline__ static void pass(int p, float2* v, float2* buf, const float2* tw, int t,
+                                              int bar_id = 0) {
     if (p > 0) {
       const float2* twp = tw + (p - 1) * N;
 #pragma unroll
@@ -329,25 +345,25 @@ struct LoopFFT {
 #pragma unroll
         for (int r = 0; r < R; ++r) buf[f(base + (r << lg))] = v[b * R + r];
       }
-      __syncwarp();
+      group_sync<T>(bar_id);
 #pragma unroll
       for (int b = 0; b < B; ++b) {
         const int j = t + b * T;
 #pragma unroll
         for (int r = 0; r < R; ++r) v[b * R + r] = buf[f(j + r * (N / R))];
       }
-      __syncwarp();
+      group_sync<T>(bar_id);
     }
   }
 
-  __device__ __forceinline__ static void run_fwd(float2* v, float2* buf, const float2* tw, int t) {
+  __device__ __forceinline__ static void run_fwd(float2* v, float2* buf, const float2* tw, int t, int bar_id = 0) {
 #pragma unroll 1
-    for (int p = 0; p < NP; ++p) pass(p, v, buf, tw, t);
+    for (int p = 0; p < NP; ++p) pass(p, v, buf, tw, t, bar_id);
   }
-  __device__ __forceinline__ static void run_inv(float2* v, float2* buf, const float2* tw, int t) {
+  __device__ __forceinline__ static void run_inv(float2* v, float2* buf, const float2* tw, int t, int bar_id = 0) {
     conj_all(v, PTS);
 #pragma unroll 1
-    for (int p = 0; p < NP; ++p) pass(p, v, buf, tw, t);
+    for (int p = 0; p < NP; ++p) pass(p, v, buf, tw, t, bar_id);
     conj_all(v, PTS);
   }
 };
