@@ -53,6 +53,8 @@ enum {
 #define BPM_FLAG_SYNC          0x1u  /* every call synchronises and reports device errors */
 #define BPM_FLAG_MULTI_LAUNCH  0x2u  /* one kernel launch per half-step instead of the
                                         persistent kernel (comparison path)           */
+#define BPM_FLAG_GRAPH         0x4u  /* batched plans: capture the launch in a CUDA graph
+                                        once per argument set and replay it          */
 
 typedef struct bpm_plan_s *bpm_plan_t;
 
@@ -86,8 +88,13 @@ int bpm_plan(bpm_plan_t *out, const bpm_instance_desc *inst, int n_inst, unsigne
 /* bpm_propagate - run slices [z_begin, z_end) of every instance (clamped to
  * [0, nz_i)), i.e. the split-step loop of the method paragraph: per slice the
  * forward 2D DFT, the propagator multiply, the inverse 2D DFT, the phase screen
- * exp(i k0 dn dz) and the intensity |E|^2.  The whole loop of an instance runs
- * in one persistent kernel launch (unless BPM_FLAG_MULTI_LAUNCH).
+ * exp(i k0 dn dz) and the intensity |E|^2.  A single-instance plan runs the
+ * whole loop in one cooperative persistent launch in which all SMs share the
+ * field (unless BPM_FLAG_MULTI_LAUNCH).  A plan with several instances (any
+ * mix of the supported sizes) runs all of them in one persistent launch of
+ * thread-block clusters: each cluster propagates whole instances taken from a
+ * device work queue, largest first (with BPM_FLAG_GRAPH the launch and its
+ * argument upload are a CUDA graph, captured once per argument set).
  *   d_dn   : host array of n_inst device pointers; instance i reads the FP16
  *            volume [nz_i][ny][nx] (slice z at offset z*nx*ny)
  *   d_Ein  : host array of device pointers to the input fields (entrance of
@@ -177,6 +184,14 @@ const char *bpm_last_error(void);
  * memory bytes, out[3] = persistent (1) or multi-launch (0), out[4] = kernel
  * launches per bpm_propagate call. */
 int bpm_plan_info(bpm_plan_t p, int *out, int n_out);
+
+/* bpm_autotune - batched plans: time the propagation of slices [0, z_probe)
+ * of every instance with each cluster size (2, 4, 8, 16 CTAs per team) on the
+ * given buffers and keep the fastest for later calls.  Overwrites d_Eout and
+ * the first z_probe intensity slices; synchronises the stream.  A no-op for
+ * single-instance plans.  Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
+int bpm_autotune(bpm_plan_t p, const void *const *d_dn, const void *const *d_Ein, void *const *d_Eout,
+                 float *const *d_I, int z_probe, cudaStream_t stream);
 
 /* bpm_debug_set_barrier_timeout - test hook: device barrier wait limit in
  * nanoseconds for this plan (default 2e9), and an extra count added to the

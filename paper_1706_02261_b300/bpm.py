@@ -28,6 +28,7 @@ BPM_ERR_NAN = -5
 BPM_ERR_UNSUPPORTED = -6
 BPM_FLAG_SYNC = 0x1
 BPM_FLAG_MULTI_LAUNCH = 0x2
+BPM_FLAG_GRAPH = 0x4
 
 SUPPORTED_N = (64, 128, 192, 256, 384, 512, 1024)
 
@@ -60,9 +61,10 @@ _lib.bpm_free.argtypes = [_vp]
 _lib.bpm_last_error.restype = ctypes.c_char_p
 _lib.bpm_plan_info.argtypes = [_vp, ctypes.POINTER(_i), _i]
 _lib.bpm_debug_set_barrier_timeout.argtypes = [_vp, ctypes.c_ulonglong, _u]
+_lib.bpm_autotune.argtypes = [_vp, _pp, _pp, _pp, _pp, _i, _vp]
 _lib.bpm_propagate_static.argtypes = [ctypes.POINTER(bpm_instance_desc), _vp, _vp, _vp, _vp, _i, _i, _vp]
 for _f in ("bpm_plan", "bpm_propagate", "bpm_multiplex_psf", "bpm_light_sheet", "bpm_check",
-           "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout", "bpm_propagate_static"):
+           "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout", "bpm_propagate_static", "bpm_autotune"):
     getattr(_lib, _f).restype = _i
 
 
@@ -143,6 +145,15 @@ def bpm_propagate(plan, dn, e_in, e_out, inten=None, z_begin: int = 0, z_end: in
     a_out = _arr([_ptr(t) for t in e_out])
     a_i = _arr([_ptr(t) if t is not None else ctypes.c_void_p(0) for t in inten]) if inten is not None else None
     return _check(_lib.bpm_propagate(plan, a_dn, a_in, a_out, a_i, z_begin, z_end, _stream_handle(stream)))
+
+
+def bpm_autotune(plan, dn, e_in, e_out, inten=None, z_probe: int = 8, stream=None) -> int:
+    """Pick the fastest cluster size of a batched plan on these buffers (lists, one entry per instance)."""
+    a_dn = _arr([_ptr(t) for t in dn])
+    a_in = _arr([_ptr(t) for t in e_in])
+    a_out = _arr([_ptr(t) for t in e_out])
+    a_i = _arr([_ptr(t) if t is not None else ctypes.c_void_p(0) for t in inten]) if inten is not None else None
+    return _check(_lib.bpm_autotune(plan, a_dn, a_in, a_out, a_i, z_probe, _stream_handle(stream)))
 
 
 def bpm_multiplex_psf(plan, inst: int, xyz: np.ndarray, phase: np.ndarray, NA: float, e_out,

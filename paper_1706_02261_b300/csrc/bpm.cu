@@ -133,6 +133,17 @@ struct bpm_plan_s {
   unsigned long long timeout_ns = 2000000000ull;
   unsigned bar_extra = 0;
   cudaStream_t last = 0;
+  // batched plans (n_inst > 1): one persistent cluster launch
+  InstArgs* d_inst = nullptr;
+  InstArgs* h_inst = nullptr;       // pinned staging of the per-call instance arguments
+  int* d_order = nullptr;
+  unsigned* d_queue = nullptr;
+  int* d_slots = nullptr;
+  size_t batch_smem = 0;
+  int cluster = 8;                  // CTAs per team (cluster size), set by bpm_autotune
+  bool have_args = false;           // h_inst holds the arguments of the last call
+  cudaStream_t cap = nullptr;       // capture stream for BPM_FLAG_GRAPH
+  cudaGraphExec_t gexec = nullptr;
 };
 
 namespace {
@@ -219,6 +230,13 @@ void free_plan(bpm_plan_s* p) {
   cudaFree(p->npupil);
   cudaFree(p->foci_idx);
   cudaFree(p->foci_phase);
+  cudaFree(p->d_inst);
+  cudaFree(p->d_order);
+  cudaFree(p->d_queue);
+  cudaFree(p->d_slots);
+  if (p->h_inst) cudaFreeHost(p->h_inst);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->cap) cudaStreamDestroy(p->cap);
   delete p;
 }
 
@@ -313,6 +331,147 @@ int finish_call(bpm_plan_s* p, cudaStream_t s) {
   return BPM_OK;
 }
 
+// ---- batched plans -------------------------------------------------------------
+
+// Work estimate of one instance: slices x (transform work of one slice).
+double instance_cost(const bpm_instance_desc& d) {
+  const double M = (double)d.nx * d.ny;
+  return (double)d.nz * M * std::log2(M);
+}
+
+int max_active_clusters(bpm_plan_s* p, int cl, int* out) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(cl * std::max(1, p->sms / cl));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = p->batch_smem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BPM_CU(cudaOccupancyMaxActiveClusters(out, (void*)bpm_batch_kernel, &cfg));
+  return BPM_OK;
+}
+
+int setup_batch(bpm_plan_s* p) {
+  const int n = (int)p->inst.size();
+  size_t smem = 0;
+  for (auto& kv : p->res) smem = std::max(smem, kv.second.smem);
+  p->batch_smem = smem;
+  BPM_CU(cudaFuncSetAttribute(bpm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  BPM_CU(cudaMalloc(&p->d_inst, sizeof(InstArgs) * n));
+  BPM_CU(cudaMalloc(&p->d_order, sizeof(int) * n));
+  BPM_CU(cudaMalloc(&p->d_queue, sizeof(unsigned)));
+  BPM_CU(cudaMalloc(&p->d_slots, sizeof(int) * 1024));
+  BPM_CU(cudaMallocHost(&p->h_inst, sizeof(InstArgs) * n));
+  std::memset(p->h_inst, 0, sizeof(InstArgs) * n);
+  // queue order: largest work first (longest-processing-time-first list
+  // scheduling over the clusters that pull from the queue)
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return instance_cost(p->inst[a].d) > instance_cost(p->inst[b].d);
+  });
+  BPM_CU(cudaMemcpy(p->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  int clusters = 0;
+  int rc = max_active_clusters(p, p->cluster, &clusters);
+  if (rc) return rc;
+  if (clusters < 1) return fail(BPM_ERR_UNSUPPORTED, "batched kernel: no cluster of %d CTAs fits", p->cluster);
+  return BPM_OK;
+}
+
+// Enqueue the batched launch: instance arguments (from pinned host memory),
+// queue reset, cluster launch.
+int enqueue_batch(bpm_plan_s* p, int clusters, cudaStream_t s) {
+  const int n = (int)p->inst.size();
+  BPM_CU(cudaMemcpyAsync(p->d_inst, p->h_inst, sizeof(InstArgs) * n, cudaMemcpyHostToDevice, s));
+  BPM_CU(cudaMemsetAsync(p->d_queue, 0, sizeof(unsigned), s));
+  BatchArgs b;
+  b.inst = p->d_inst;
+  b.order = p->d_order;
+  b.n_inst = n;
+  b.queue = p->d_queue;
+  b.slots = p->d_slots;
+  b.err = p->err;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = p->cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(clusters * p->cluster);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = p->batch_smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BPM_CU(cudaLaunchKernelEx(&cfg, bpm_batch_kernel, b));
+  return BPM_OK;
+}
+
+int propagate_batch(bpm_plan_s* p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
+                    float* const* d_I, int z_begin, int z_end, cudaStream_t stream) {
+  const int n = (int)p->inst.size();
+  std::vector<InstArgs> args(n);
+  std::memset(args.data(), 0, sizeof(InstArgs) * n);
+  for (int i = 0; i < n; ++i) {
+    const InstPlan& in = p->inst[i];
+    const NRes& r = p->res[in.d.nx];
+    InstArgs& a = args[i];
+    a.work = static_cast<float2*>(d_Eout[i]);
+    a.ein = static_cast<const float2*>(d_Ein[i]);
+    a.dn = static_cast<const __half*>(d_dn[i]);
+    a.inten = d_I ? d_I[i] : nullptr;
+    a.ht = in.ht;
+    a.tw = r.tw;
+    const double k0 = kTwoPi / in.d.lambda;
+    a.screen_c = (float)(k0 * in.d.dz);
+    a.n = in.d.nx;
+    a.z_begin = std::min(z_begin, in.d.nz);
+    a.z_end = std::min(z_end, in.d.nz);
+    const double ph = std::fmod(k0 * in.d.n0 * in.d.dz * (double)(a.z_end - a.z_begin), kTwoPi);
+    a.carrier = make_float2((float)std::cos(ph), (float)std::sin(ph));
+  }
+  const bool same = p->have_args && std::memcmp(args.data(), p->h_inst, sizeof(InstArgs) * n) == 0;
+  if (!same) {
+    // the pinned staging may still feed an earlier launch on this stream
+    BPM_CU(cudaStreamSynchronize(p->last));
+    BPM_CU(cudaStreamSynchronize(stream));
+    std::memcpy(p->h_inst, args.data(), sizeof(InstArgs) * n);
+    p->have_args = true;
+    if (p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+  }
+  int clusters = 0;
+  int rc0 = max_active_clusters(p, p->cluster, &clusters);
+  if (rc0) return rc0;
+  if (clusters < 1) return fail(BPM_ERR_UNSUPPORTED, "batched kernel: no cluster of %d CTAs fits", p->cluster);
+  clusters = std::min(clusters, 1024);
+  if (!(p->flags & BPM_FLAG_GRAPH)) return enqueue_batch(p, clusters, stream);
+  if (!p->gexec) {
+    if (!p->cap) BPM_CU(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+    BPM_CU(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_batch(p, clusters, p->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(BPM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&p->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(BPM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  BPM_CU(cudaGraphLaunch(p->gexec, stream));
+  return BPM_OK;
+}
+
 }  // namespace
 
 // ---- C ABI -------------------------------------------------------------------
@@ -322,7 +481,8 @@ extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_in
   if (!out) return fail(BPM_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!inst || n_inst < 1 || n_inst > 4096) return fail(BPM_ERR_ARG, "n_inst must be in [1, 4096]");
-  if (flags & ~(BPM_FLAG_SYNC | BPM_FLAG_MULTI_LAUNCH)) return fail(BPM_ERR_ARG, "unknown flag bits 0x%x", flags);
+  if (flags & ~(BPM_FLAG_SYNC | BPM_FLAG_MULTI_LAUNCH | BPM_FLAG_GRAPH))
+    return fail(BPM_ERR_ARG, "unknown flag bits 0x%x", flags);
   for (int i = 0; i < n_inst; ++i) {
     int rc = check_desc(inst[i], i);
     if (rc) return rc;
@@ -359,6 +519,7 @@ extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_in
         ip.ht, inst[i].nx, inst[i].ny, inst[i].dx, inst[i].dy, inst[i].dz, inst[i].lambda, inst[i].n0);
     cu(cudaGetLastError(), "bpm_build_ht_kernel");
   }
+  if (rc == BPM_OK && n_inst > 1) rc = setup_batch(p);
   if (rc == BPM_OK) cu(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
   if (rc != BPM_OK) {
     free_plan(p);
@@ -381,6 +542,11 @@ extern "C" int bpm_propagate(bpm_plan_t p, const void* const* d_dn, const void* 
       return fail(BPM_ERR_ARG, "instance %zu: NULL device pointer", i);
     if (!aligned16(d_Ein[i]) || !aligned16(d_Eout[i]) || !aligned16(d_dn[i]) || (d_I && !aligned16(d_I[i])))
       return fail(BPM_ERR_ALIGN, "instance %zu: device pointers must be 16-byte aligned", i);
+  }
+  if (p->inst.size() > 1) {
+    int rc = propagate_batch(p, d_dn, d_Ein, d_Eout, d_I, z_begin, z_end, stream);
+    if (rc) return rc;
+    return finish_call(p, stream);
   }
   for (size_t i = 0; i < p->inst.size(); ++i) {
     const InstPlan& in = p->inst[i];
@@ -541,8 +707,58 @@ extern "C" int bpm_plan_info(bpm_plan_t p, int* out, int n_out) {
   const bool multi = (p->flags & BPM_FLAG_MULTI_LAUNCH) != 0;
   const int nz = p->inst[0].d.nz;
   int vals[5] = {r.team, kThreads, (int)(multi ? r.smem : r.smem_persist), multi ? 0 : 1, multi ? 1 + 2 * nz : 1};
+  if (p->inst.size() > 1) {
+    vals[0] = p->cluster;
+    vals[2] = (int)p->batch_smem;
+    vals[3] = 1;
+    vals[4] = 1;
+  }
   for (int i = 0; i < n_out && i < 5; ++i) out[i] = vals[i];
   return BPM_OK;
+}
+
+extern "C" int bpm_autotune(bpm_plan_t p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
+                            float* const* d_I, int z_probe, cudaStream_t stream) {
+  if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
+  if (p->inst.size() < 2) return BPM_OK;     // single-field plans have one configuration
+  if (z_probe < 1) return fail(BPM_ERR_ARG, "z_probe must be >= 1");
+  const int keep = p->cluster;
+  const unsigned keep_flags = p->flags;
+  p->flags &= ~(unsigned)BPM_FLAG_GRAPH;
+  float best = 1e30f;
+  int best_cl = keep;
+  cudaEvent_t e0, e1;
+  BPM_CU(cudaEventCreate(&e0));
+  BPM_CU(cudaEventCreate(&e1));
+  for (int cl : {2, 4, 8, 16}) {
+    int clusters = 0;
+    p->cluster = cl;
+    if (max_active_clusters(p, cl, &clusters) != BPM_OK || clusters < 1) continue;
+    int rc = bpm_propagate(p, d_dn, d_Ein, d_Eout, d_I, 0, z_probe, stream);   // warm-up
+    if (rc == BPM_OK) {
+      cudaEventRecord(e0, stream);
+      rc = bpm_propagate(p, d_dn, d_Ein, d_Eout, d_I, 0, z_probe, stream);
+      cudaEventRecord(e1, stream);
+    }
+    if (rc != BPM_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_cl = cl;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  p->cluster = best_cl;
+  p->flags = keep_flags;
+  p->have_args = false;
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  return bpm_check(p);
 }
 
 extern "C" int bpm_debug_set_barrier_timeout(bpm_plan_t p, unsigned long long timeout_ns, unsigned extra) {

@@ -783,4 +783,120 @@ __global__ void bpm_build_ht_kernel(float2* ht, int nx, int ny, double dx, doubl
   ht[i] = h;
 }
 
+// ---------------------------------------------------------------------------
+// batched propagation: many independent instances, one persistent launch
+// ---------------------------------------------------------------------------
+// Every thread-block cluster is a team: it takes the next instance from a
+// device work queue (instances are queued largest first), runs all of that
+// instance's slices with the cluster's hardware barrier between half-steps
+// (release/acquire at cluster scope, so the field exchanged through L2 is
+// visible), then takes the next one.  No grid-wide barrier is involved, so
+// clusters run independently and instances of different sizes mix freely.
+struct InstArgs {
+  float2* work;
+  const float2* ein;
+  const __half* dn;
+  float* inten;
+  const float2* ht;
+  const float2* tw;
+  float screen_c;
+  float2 carrier;
+  int n, z_begin, z_end;
+};
+
+struct BatchArgs {
+  const InstArgs* inst;   // [n_inst]
+  const int* order;       // queue order (instance indices, largest first)
+  int n_inst;
+  unsigned* queue;        // work counter, zeroed before the launch
+  int* slots;             // per-cluster broadcast of the fetched queue position
+  int* err;
+};
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+
+template <int N>
+__device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int rank, int CL, float2* smem,
+                                               bool& bad) {
+  using C = Cfg<N>;
+  float2* s_twf = smem;
+  float2* s_twi = s_twf + C::TWF;
+  float2* s_buf = s_twi + C::TWI;
+  StepArgs a;
+  a.work = ia.work;
+  a.ein = ia.ein;
+  a.dn = ia.dn;
+  a.inten = ia.inten;
+  a.ht = ia.ht;
+  a.tw = ia.tw;
+  a.screen_c = ia.screen_c;
+  a.carrier = ia.carrier;
+  a.z_begin = ia.z_begin;
+  a.z_end = ia.z_end;
+  a.err = err;
+  a.accumulate = 0;
+  a.out = nullptr;
+  const int lo = (rank * N) / CL, hi = ((rank + 1) * N) / CL;
+  if (a.z_end <= a.z_begin) {
+    // empty slice range: the output is the input
+    if (a.work != a.ein)
+      for (int i = lo * N + threadIdx.x; i < hi * N; i += kThreads) __stcg(a.work + i, __ldcg(a.ein + i));
+    cluster_sync_all();
+    return;
+  }
+  load_twiddles<N>(a, s_twf, s_twi);
+  row_half_step<N, ROW_FWD>(a, lo, hi, a.z_begin, s_buf, s_twf, s_twi, bad);
+  cluster_sync_all();
+  for (int z = a.z_begin; z < a.z_end; ++z) {
+    col_half_step<N, COL_PROP>(a, lo, hi, s_buf, s_twf, s_twi);
+    cluster_sync_all();
+    if (z + 1 < a.z_end) row_half_step<N, ROW_STEP>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+    else row_half_step<N, ROW_LAST>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+    cluster_sync_all();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) bpm_batch_kernel(BatchArgs b) {
+  extern __shared__ float4 smem_f4[];
+  float2* smem = reinterpret_cast<float2*>(smem_f4);
+  const int CL = (int)cluster_size(), rank = (int)cluster_rank(), cid = (int)cluster_id();
+  bool bad = false;
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) b.slots[cid] = (int)atomicAdd(b.queue, 1u);
+    cluster_sync_all();
+    const int k = ld_volatile(b.slots + cid);
+    cluster_sync_all();     // every CTA has read the slot before the leader may overwrite it
+    if (k >= b.n_inst) break;
+    const InstArgs ia = b.inst[b.order[k]];
+    switch (ia.n) {
+      case 64: batch_instance<64>(ia, b.err, rank, CL, smem, bad); break;
+      case 128: batch_instance<128>(ia, b.err, rank, CL, smem, bad); break;
+      case 192: batch_instance<192>(ia, b.err, rank, CL, smem, bad); break;
+      case 256: batch_instance<256>(ia, b.err, rank, CL, smem, bad); break;
+      case 384: batch_instance<384>(ia, b.err, rank, CL, smem, bad); break;
+      case 512: batch_instance<512>(ia, b.err, rank, CL, smem, bad); break;
+      case 1024: batch_instance<1024>(ia, b.err, rank, CL, smem, bad); break;
+      default: break;
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(b.err, 0, kDevErrNan);
+}
+
 }  // namespace bpmk
