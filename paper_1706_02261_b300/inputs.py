@@ -241,3 +241,37 @@ def batch_64(count: int = 64, seed: int = 3) -> list:
 def dn_to_f64(dn16: np.ndarray) -> np.ndarray:
     """Exact widening of the FP16 index volume for the FP64 oracle."""
     return dn16.astype(np.float64)
+
+
+# --------------------------------------------------------------------------
+# corrector network: parameter layout and seeded initial values
+# --------------------------------------------------------------------------
+
+CORRECTOR_CHANNELS = 32
+
+
+def corrector_layer_shapes(c_in: int):
+    """(C_out, C_in) of the corrector's four 3 x 3 convolutions."""
+    c = CORRECTOR_CHANNELS
+    return [(c, c_in), (c, c), (c, c), (2, c)]
+
+
+def corrector_param_count(c_in: int) -> int:
+    return sum(o * i * 9 + o for o, i in corrector_layer_shapes(c_in))
+
+
+def corrector_init(c_in: int, seed: int) -> np.ndarray:
+    """Flat initial parameters [W1, b1, ..., W4, b4] (weights [o][i][3][3]):
+    He-normal weights for the first three layers, zero biases, and a zero last
+    layer so the untrained residual corrector is the identity.  Drawn from
+    ``default_rng(seed)`` layer by layer."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    shapes = corrector_layer_shapes(c_in)
+    for k, (o, i) in enumerate(shapes):
+        if k < len(shapes) - 1:
+            W = rng.standard_normal((o, i, 3, 3)) * np.sqrt(2.0 / (9 * i))
+        else:
+            W = np.zeros((o, i, 3, 3))
+        parts += [W.ravel(), np.zeros(o)]
+    return np.concatenate(parts)
