@@ -18,6 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbpm.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "bpm.h")
+HEADERS = [HEADER, os.path.join(os.path.dirname(_HERE), "include", "bpm_corrector.h")]
 
 BPM_OK = 0
 BPM_ERR_ARG = -1
@@ -69,8 +70,8 @@ for _f in ("bpm_plan", "bpm_propagate", "bpm_multiplex_psf", "bpm_light_sheet", 
 
 
 def declared_symbols() -> list:
-    """Names of the functions declared in include/bpm.h."""
-    txt = open(HEADER).read()
+    """Names of the functions declared in include/bpm.h and include/bpm_corrector.h."""
+    txt = "".join(open(h).read() for h in HEADERS)
     return sorted(set(re.findall(r"^(?:int|const char \*)\s*(bpm_\w+)\s*\(", txt, re.M)))
 
 
@@ -196,3 +197,93 @@ def bpm_propagate_static(instance: "Instance", dn, e_in, e_out, inten=None, z_be
     desc = instance.desc()
     return _check(_lib.bpm_propagate_static(ctypes.byref(desc), _ptr(dn), _ptr(e_in), _ptr(e_out),
                                             _ptr(inten), z_begin, z_end, _stream_handle(stream)))
+
+
+# ---- learned coarse-step corrector (include/bpm_corrector.h) ----------------
+_fp = ctypes.POINTER(ctypes.c_float)
+_lib.bpm_corrector_create.argtypes = [ctypes.POINTER(_vp), _i, _i, _i, _i, _vp]
+_lib.bpm_corrector_param_count.argtypes = [_vp]
+_lib.bpm_corrector_set_params.argtypes = [_vp, _vp, _i, _vp]
+_lib.bpm_corrector_get_params.argtypes = [_vp, _vp, _i, _i, _vp]
+_lib.bpm_corrector_forward.argtypes = [_vp, _vp, _vp, _i, _i, _i, _vp]
+_lib.bpm_corrector_loss_grad.argtypes = [_vp, _vp, _vp, _i, _i, _i, _fp, _vp]
+_lib.bpm_corrector_adam.argtypes = [_vp, ctypes.c_float, _vp]
+_lib.bpm_corrector_train_step.argtypes = [_vp, _vp, _vp, _i, _i, _i, ctypes.c_float, _fp, _vp]
+_lib.bpm_corrector_pack.argtypes = [_vp, _vp, _vp, ctypes.c_float, _vp, _i, _i, _i, _vp]
+_lib.bpm_corrector_apply.argtypes = [_vp, _vp, _vp, ctypes.c_float, _i, _i, _vp]
+_lib.bpm_coarsen_index.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp]
+_lib.bpm_corrector_free.argtypes = [_vp]
+_lib.bpm_corrector_last_error.restype = ctypes.c_char_p
+for _f in ("bpm_corrector_create", "bpm_corrector_param_count", "bpm_corrector_set_params",
+           "bpm_corrector_get_params", "bpm_corrector_forward", "bpm_corrector_loss_grad", "bpm_corrector_adam",
+           "bpm_corrector_train_step", "bpm_corrector_pack", "bpm_corrector_apply", "bpm_coarsen_index",
+           "bpm_corrector_free"):
+    getattr(_lib, _f).restype = _i
+
+
+def _ccheck(rc: int):
+    if rc != BPM_OK:
+        raise BpmError(rc, _lib.bpm_corrector_last_error().decode())
+    return rc
+
+
+class Corrector:
+    """Owner of a bpm_corrector_t (argument marshalling only)."""
+
+    def __init__(self, in_channels: int, max_batch: int, max_h: int, max_w: int, stream=None):
+        self.h = ctypes.c_void_p()
+        _ccheck(_lib.bpm_corrector_create(ctypes.byref(self.h), in_channels, max_batch, max_h, max_w,
+                                          _stream_handle(stream)))
+        self.in_channels = in_channels
+        self.n_params = _lib.bpm_corrector_param_count(self.h)
+
+    def set_params(self, theta: np.ndarray, stream=None):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        assert a.size == self.n_params
+        _ccheck(_lib.bpm_corrector_set_params(self.h, ctypes.c_void_p(a.ctypes.data), a.size, _stream_handle(stream)))
+
+    def get_params(self, which: int = 0, stream=None) -> np.ndarray:
+        a = np.zeros(self.n_params, np.float32)
+        _ccheck(_lib.bpm_corrector_get_params(self.h, ctypes.c_void_p(a.ctypes.data), a.size, which,
+                                              _stream_handle(stream)))
+        return a
+
+    def forward(self, x, out, stream=None):
+        b, _, hh, ww = x.shape
+        _ccheck(_lib.bpm_corrector_forward(self.h, _ptr(x), _ptr(out), b, hh, ww, _stream_handle(stream)))
+
+    def loss_grad(self, x, target, stream=None) -> float:
+        b, _, hh, ww = x.shape
+        loss = ctypes.c_float()
+        _ccheck(_lib.bpm_corrector_loss_grad(self.h, _ptr(x), _ptr(target), b, hh, ww, ctypes.byref(loss),
+                                             _stream_handle(stream)))
+        return float(loss.value)
+
+    def adam(self, lr: float, stream=None):
+        _ccheck(_lib.bpm_corrector_adam(self.h, lr, _stream_handle(stream)))
+
+    def train_step(self, x, target, lr: float, want_loss: bool = False, stream=None):
+        b, _, hh, ww = x.shape
+        loss = ctypes.c_float()
+        _ccheck(_lib.bpm_corrector_train_step(self.h, _ptr(x), _ptr(target), b, hh, ww, lr,
+                                              ctypes.byref(loss) if want_loss else None, _stream_handle(stream)))
+        return float(loss.value) if want_loss else None
+
+    def pack(self, fields, dn, dn_scale: float, x, stream=None):
+        b, hh, ww = fields.shape
+        _ccheck(_lib.bpm_corrector_pack(self.h, _ptr(fields), _ptr(dn), dn_scale, _ptr(x), b, hh, ww,
+                                        _stream_handle(stream)))
+
+    def apply(self, field, dn=None, dn_scale: float = 0.0, stream=None):
+        hh, ww = field.shape
+        _ccheck(_lib.bpm_corrector_apply(self.h, _ptr(field), _ptr(dn), dn_scale, hh, ww, _stream_handle(stream)))
+
+    def free(self):
+        if self.h:
+            _lib.bpm_corrector_free(self.h)
+            self.h = ctypes.c_void_p()
+
+
+def bpm_coarsen_index(dn, factor: int, out, stream=None) -> int:
+    nz, ny, nx = dn.shape
+    return _ccheck(_lib.bpm_coarsen_index(_ptr(dn), nz, ny, nx, factor, _ptr(out), _stream_handle(stream)))

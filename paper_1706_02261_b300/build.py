@@ -7,9 +7,9 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "csrc", "bpm.cu")
-DEPS = [os.path.join(HERE, "csrc", f) for f in ("bpm.cu", "bpm_kernels.cuh", "fft.cuh")] + \
-       [os.path.join(ROOT, "include", "bpm.h")]
+SRCS = [os.path.join(HERE, "csrc", f) for f in ("bpm.cu", "corrector.cu")]
+DEPS = [os.path.join(HERE, "csrc", f) for f in ("bpm.cu", "corrector.cu", "bpm_kernels.cuh", "fft.cuh")] + \
+       [os.path.join(ROOT, "include", f) for f in ("bpm.h", "bpm_corrector.h")]
 LIB = os.path.join(HERE, "libbpm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -27,7 +27,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not needs_build():
         return LIB
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-           "-shared", "-I", os.path.join(ROOT, "include"), SRC, "-o", LIB + ".tmp", "-lcudart"]
+           "-shared", "-I", os.path.join(ROOT, "include"), *SRCS, "-o", LIB + ".tmp", "-lcudart"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)

@@ -1,0 +1,111 @@
+"""The corrector's CUDA kernels against the FP64 oracle (forward pass, loss,
+every parameter gradient, the Adam step, the coarsened index), and training
+on pairs generated by the propagation: the loss falls and, on held-out
+seeds, coarse steps with the corrector are closer to fine-step BPM than
+coarse steps without it."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import corrector as oc  # noqa: E402
+from paper_1706_02261_b300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1706_02261_b300 import bpm
+    return bpm
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("c_in", [2, 3])
+def test_forward_loss_and_gradients_match_oracle(B, c_in):
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(10 + c_in)
+    theta = inputs.corrector_init(c_in, 5) + 0.05 * rng.standard_normal(inputs.corrector_param_count(c_in))
+    bsz, h, w = 2, 32, 48
+    X = rng.standard_normal((bsz, c_in, h, w)).astype(np.float32)
+    T = rng.standard_normal((bsz, 2, h, w)).astype(np.float32)
+    corr = B.Corrector(c_in, 4, 64, 64)
+    try:
+        corr.set_params(theta.astype(np.float32))
+        work = corr.get_params(which=1).astype(np.float64)        # BF16-rounded weights used by the kernels
+        assert np.max(np.abs(work - theta)) <= 0.01 * np.max(np.abs(theta))
+        xd, td = torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev)
+        out = torch.empty((bsz, 2, h, w), dtype=torch.float32, device=dev)
+        corr.forward(xd, out)
+        ref_out, _, _ = oc.forward(work, X.astype(np.float64))
+        assert rel(out.cpu().numpy(), ref_out) <= 1e-5
+        loss = corr.loss_grad(xd, td)
+        g = corr.get_params(which=2).astype(np.float64)
+        ref_loss, ref_g = oc.loss_and_grad(work, X.astype(np.float64), T.astype(np.float64))
+        assert loss == pytest.approx(ref_loss, rel=1e-5)
+        k = 0
+        for o, i in oc.layer_shapes(c_in):       # every layer's weights and biases
+            for size in (o * i * 9, o):
+                assert rel(g[k:k + size], ref_g[k:k + size]) <= 1e-4
+                k += size
+    finally:
+        corr.free()
+
+
+def test_adam_step_matches_oracle(B):
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(3)
+    theta = inputs.corrector_init(2, 1) + 0.05 * rng.standard_normal(inputs.corrector_param_count(2))
+    X = torch.from_numpy(rng.standard_normal((2, 2, 16, 16)).astype(np.float32)).to(dev)
+    T = torch.from_numpy(rng.standard_normal((2, 2, 16, 16)).astype(np.float32)).to(dev)
+    corr = B.Corrector(2, 2, 16, 16)
+    try:
+        corr.set_params(theta.astype(np.float32))
+        m = np.zeros(theta.size)
+        v = np.zeros(theta.size)
+        th = corr.get_params(0).astype(np.float64)
+        for t in (1, 2):
+            corr.loss_grad(X, T)
+            g = corr.get_params(2).astype(np.float64)
+            corr.adam(1e-3)
+            th, m, v = oc.adam_step(th, g, m, v, t, 1e-3)
+            got = corr.get_params(0).astype(np.float64)
+            assert np.max(np.abs(got - th)) <= 1e-6 * max(1.0, np.max(np.abs(th)))
+    finally:
+        corr.free()
+
+
+def test_coarsen_index(B):
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(4)
+    dn = rng.uniform(0, 0.05, size=(10, 32, 48)).astype(np.float16)
+    out = torch.empty((2, 32, 48), dtype=torch.float16, device=dev)
+    B.bpm_coarsen_index(torch.from_numpy(dn).to(dev), 4, out)
+    torch.cuda.synchronize()
+    ref = dn[:8].astype(np.float64).reshape(2, 4, 32, 48).mean(axis=1)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 2 ** -11 * 0.05      # within FP16 rounding at |dn| <= 0.05
+
+
+def test_training_gains_over_coarse_steps_on_held_out_seeds(B):
+    from paper_1706_02261_b300 import corrector as C
+    dev = torch.device("cuda")
+    s = C.Setup(n=128, nz=64, c_in=3)
+    corr = B.Corrector(s.c_in, 16, s.n, s.n)
+    try:
+        corr.set_params(inputs.corrector_init(s.c_in, 0).astype(np.float32))
+        X, T = C.make_pairs(s, range(4000, 4024), corr, dev)
+        losses = C.train(corr, X, T, steps=600, batch=16, lr=1e-3, seed=1, log_every=50)
+        first = np.mean([l for _, l in losses[:2]])
+        last = np.mean([l for _, l in losses[-2:]])
+        assert last < 0.7 * first, losses
+        ev = C.evaluate(s, [5000, 5001, 5002], corr, dev)
+        gain = np.mean([r["coarse"] for r in ev]) / np.mean([r["corrected"] for r in ev])
+        print("held-out errors", ev, "gain", gain)
+        assert gain > 1.0, ev
+    finally:
+        corr.free()
