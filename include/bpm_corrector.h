@@ -7,7 +7,7 @@
  * after each coarse step, E <- E + f(E): four 3x3 convolutions with circular
  * padding (C_in -> 32 -> 32 -> 32 -> 2, ReLU between), input channels
  * Re E, Im E and optionally the averaged index step (times a caller scale),
- * output the correction of Re E and Im E.  It is trained on pairs (one coarse
+ * output the correction of Re E and Im E (times a fixed residual scale).  It is trained on pairs (one coarse
  * step from a fine-step field at plane 4j, the fine-step field at plane 4j+4)
  * that the propagation itself generates.  The paper has no network: it only
  * motivates wave-optical simulations as training data for machine learning
@@ -43,6 +43,11 @@ int bpm_corrector_create(bpm_corrector_t *out, int in_channels, int max_batch, i
 /* Number of parameters (flat vector length). */
 int bpm_corrector_param_count(bpm_corrector_t c);
 
+/* Residual scale sigma (default 1): the network output is
+ * x[:, :2] + sigma f(x).  Set it to the RMS size of the corrections to be
+ * learned so that f is of order one. */
+int bpm_corrector_set_residual_scale(bpm_corrector_t c, float sigma);
+
 /* Load FP32 master parameters (n = param count), reset the Adam moments and
  * the step counter; synchronises the stream. */
 int bpm_corrector_set_params(bpm_corrector_t c, const float *h_params, int n, cudaStream_t stream);
@@ -52,11 +57,11 @@ int bpm_corrector_set_params(bpm_corrector_t c, const float *h_params, int n, cu
  * synchronises the stream. */
 int bpm_corrector_get_params(bpm_corrector_t c, float *h_params, int n, int which, cudaStream_t stream);
 
-/* d_out[b] = d_x[b][0:2] + f(d_x[b]); d_x [batch][C_in][h][w], d_out [batch][2][h][w]. */
+/* d_out[b] = d_x[b][0:2] + sigma f(d_x[b]); d_x [batch][C_in][h][w], d_out [batch][2][h][w]. */
 int bpm_corrector_forward(bpm_corrector_t c, const float *d_x, float *d_out, int batch, int h, int w,
                           cudaStream_t stream);
 
-/* Mean squared error L = sum (x[:, :2] + f(x) - target)^2 / numel(target) and
+/* Mean squared error L = sum (x[:, :2] + sigma f(x) - target)^2 / numel(target) and
  * its gradient with respect to every parameter (kept in the corrector);
  * h_loss (nullable) receives L, which synchronises the stream. */
 int bpm_corrector_loss_grad(bpm_corrector_t c, const float *d_x, const float *d_target, int batch, int h, int w,
@@ -70,14 +75,19 @@ int bpm_corrector_adam(bpm_corrector_t c, float lr, cudaStream_t stream);
 int bpm_corrector_train_step(bpm_corrector_t c, const float *d_x, const float *d_target, int batch, int h, int w,
                              float lr, float *h_loss, cudaStream_t stream);
 
-/* Pack complex float fields [batch][h][w] (and, for 3 input channels, an FP16
- * index plane per field times dn_scale, or zeros when d_dn is NULL) into the
- * network layout d_x [batch][C_in][h][w]. */
-int bpm_corrector_pack(bpm_corrector_t c, const void *d_fields, const void *d_dn, float dn_scale, float *d_x,
-                       int batch, int h, int w, cudaStream_t stream);
+/* Pack complex float fields [batch][h][w] into the network layout d_x
+ * [batch][C_in][h][w]: each field divided by its RMS amplitude a_b (so the
+ * correction scales linearly with the field, as the splitting error does),
+ * and for 3 input channels the FP16 index plane of the field times dn_scale
+ * (zeros when d_dn is NULL).  When d_targets (complex [batch][h][w]) is given,
+ * d_t [batch][2][h][w] receives the targets divided by the same a_b.
+ * batch <= the corrector's max_batch. */
+int bpm_corrector_pack(bpm_corrector_t c, const void *d_fields, const void *d_targets, const void *d_dn,
+                       float dn_scale, float *d_x, float *d_t, int batch, int h, int w, cudaStream_t stream);
 
-/* In place on one complex float field [h][w]: E <- E + f(E) (d_dn: the
- * coarse step's averaged index plane for 3-channel correctors, else NULL). */
+/* In place on one complex float field [h][w]: E <- E + a sigma f(E / a),
+ * a the RMS amplitude of E (d_dn: the coarse step's averaged index plane for
+ * 3-channel correctors, else NULL). */
 int bpm_corrector_apply(bpm_corrector_t c, void *d_field, const void *d_dn, float dn_scale, int h, int w,
                         cudaStream_t stream);
 

@@ -12,7 +12,10 @@ step, and
     Z2 = conv(A1; W2, b2),  A2 = relu(Z2)          (32 -> 32)
     Z3 = conv(A2; W3, b3),  A3 = relu(Z3)          (32 -> 32)
     Z4 = conv(A3; W4, b4)                          (32 -> 2)
-    out = X[:, :2] + Z4                            (residual correction)
+    out = X[:, :2] + sigma Z4                      (residual correction)
+
+sigma is a fixed residual scale (the RMS size of the corrections the network
+is trained to make, so that its outputs are of order one).
 
 where conv is a 3 x 3 cross-correlation with periodic (circular) padding,
 matching the periodic boundaries of the propagation:
@@ -99,7 +102,7 @@ def conv_weight_grad(X: np.ndarray, dY: np.ndarray):
     return dW, dY.sum(axis=(0, 2, 3))
 
 
-def forward(theta: np.ndarray, X: np.ndarray):
+def forward(theta: np.ndarray, X: np.ndarray, sigma: float = 1.0):
     """Network output and the intermediate tensors backpropagation needs."""
     c_in = X.shape[1]
     layers = unflatten(theta, c_in)
@@ -110,18 +113,18 @@ def forward(theta: np.ndarray, X: np.ndarray):
         pre.append(Z)
         A = np.maximum(Z, 0.0) if k < LAYERS - 1 else Z
         acts.append(A)
-    out = X[:, :2] + pre[-1]
+    out = X[:, :2] + sigma * pre[-1]
     return out, acts, pre
 
 
-def loss_and_grad(theta: np.ndarray, X: np.ndarray, T: np.ndarray):
+def loss_and_grad(theta: np.ndarray, X: np.ndarray, T: np.ndarray, sigma: float = 1.0):
     """Mean squared error and its gradient with respect to the flat parameters."""
     c_in = X.shape[1]
     layers = unflatten(theta, c_in)
-    out, acts, pre = forward(theta, X)
+    out, acts, pre = forward(theta, X, sigma)
     r = out - T
     loss = float(np.sum(r * r) / r.size)
-    dZ = 2.0 * r / r.size                    # d loss / d Z4 (the residual path adds X)
+    dZ = 2.0 * sigma * r / r.size            # d loss / d Z4 (the residual path adds X)
     grads = [None] * LAYERS
     for k in range(LAYERS - 1, -1, -1):
         W, _ = layers[k]

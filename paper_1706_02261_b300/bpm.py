@@ -203,13 +203,14 @@ def bpm_propagate_static(instance: "Instance", dn, e_in, e_out, inten=None, z_be
 _fp = ctypes.POINTER(ctypes.c_float)
 _lib.bpm_corrector_create.argtypes = [ctypes.POINTER(_vp), _i, _i, _i, _i, _vp]
 _lib.bpm_corrector_param_count.argtypes = [_vp]
+_lib.bpm_corrector_set_residual_scale.argtypes = [_vp, ctypes.c_float]
 _lib.bpm_corrector_set_params.argtypes = [_vp, _vp, _i, _vp]
 _lib.bpm_corrector_get_params.argtypes = [_vp, _vp, _i, _i, _vp]
 _lib.bpm_corrector_forward.argtypes = [_vp, _vp, _vp, _i, _i, _i, _vp]
 _lib.bpm_corrector_loss_grad.argtypes = [_vp, _vp, _vp, _i, _i, _i, _fp, _vp]
 _lib.bpm_corrector_adam.argtypes = [_vp, ctypes.c_float, _vp]
 _lib.bpm_corrector_train_step.argtypes = [_vp, _vp, _vp, _i, _i, _i, ctypes.c_float, _fp, _vp]
-_lib.bpm_corrector_pack.argtypes = [_vp, _vp, _vp, ctypes.c_float, _vp, _i, _i, _i, _vp]
+_lib.bpm_corrector_pack.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _i, _i, _i, _vp]
 _lib.bpm_corrector_apply.argtypes = [_vp, _vp, _vp, ctypes.c_float, _i, _i, _vp]
 _lib.bpm_coarsen_index.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp]
 _lib.bpm_corrector_free.argtypes = [_vp]
@@ -217,7 +218,7 @@ _lib.bpm_corrector_last_error.restype = ctypes.c_char_p
 for _f in ("bpm_corrector_create", "bpm_corrector_param_count", "bpm_corrector_set_params",
            "bpm_corrector_get_params", "bpm_corrector_forward", "bpm_corrector_loss_grad", "bpm_corrector_adam",
            "bpm_corrector_train_step", "bpm_corrector_pack", "bpm_corrector_apply", "bpm_coarsen_index",
-           "bpm_corrector_free"):
+           "bpm_corrector_free", "bpm_corrector_set_residual_scale"):
     getattr(_lib, _f).restype = _i
 
 
@@ -241,6 +242,9 @@ class Corrector:
         a = np.ascontiguousarray(theta, dtype=np.float32)
         assert a.size == self.n_params
         _ccheck(_lib.bpm_corrector_set_params(self.h, ctypes.c_void_p(a.ctypes.data), a.size, _stream_handle(stream)))
+
+    def set_residual_scale(self, sigma: float):
+        _ccheck(_lib.bpm_corrector_set_residual_scale(self.h, sigma))
 
     def get_params(self, which: int = 0, stream=None) -> np.ndarray:
         a = np.zeros(self.n_params, np.float32)
@@ -269,10 +273,10 @@ class Corrector:
                                               ctypes.byref(loss) if want_loss else None, _stream_handle(stream)))
         return float(loss.value) if want_loss else None
 
-    def pack(self, fields, dn, dn_scale: float, x, stream=None):
+    def pack(self, fields, dn, dn_scale: float, x, targets=None, t=None, stream=None):
         b, hh, ww = fields.shape
-        _ccheck(_lib.bpm_corrector_pack(self.h, _ptr(fields), _ptr(dn), dn_scale, _ptr(x), b, hh, ww,
-                                        _stream_handle(stream)))
+        _ccheck(_lib.bpm_corrector_pack(self.h, _ptr(fields), _ptr(targets), _ptr(dn), dn_scale, _ptr(x), _ptr(t),
+                                        b, hh, ww, _stream_handle(stream)))
 
     def apply(self, field, dn=None, dn_scale: float = 0.0, stream=None):
         hh, ww = field.shape

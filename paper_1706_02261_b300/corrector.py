@@ -6,7 +6,8 @@ method but add splitting error.  A small convolutional network f
 (include/bpm_corrector.h) corrects the field after every coarse step,
 E <- E + f(E).  Training pairs are produced by the propagation kernels
 themselves: the input is one coarse step from the fine-step field at plane 4j,
-the target is the fine-step field at plane 4j + 4.  Fine-step BPM is both the
+the target is the fine-step field at plane 4j + 4, both divided by the RMS
+amplitude of the input so the network sees fields of unit size.  Fine-step BPM is both the
 fallback and the judge of the corrector's error.
 
 This module only orchestrates calls into libbpm.so (all arithmetic runs in its
@@ -62,12 +63,6 @@ def input_field(s: Setup, seed: int, plan, dev):
     return e
 
 
-def _to_channels(fields):
-    """complex [P][h][w] -> float [P][2][h][w] (layout only)."""
-    import torch
-    return torch.view_as_real(fields).permute(0, 3, 1, 2).contiguous()
-
-
 def make_pairs(s: Setup, seeds, corr: "B.Corrector", dev):
     """Training pairs (packed coarse-step inputs X, fine targets T) for every
     coarse step of every seed's field."""
@@ -90,14 +85,26 @@ def make_pairs(s: Setup, seeds, corr: "B.Corrector", dev):
             for j in range(s.nz // FACTOR):
                 B.bpm_propagate(coarse, dnc, ein[j], ec[j], None, j, j + 1)
             x = torch.empty((ein.shape[0], s.c_in, s.n, s.n), dtype=torch.float32, device=dev)
-            corr.pack(ec, dnc if s.c_in == 3 else None, s.dn_scale, x)
+            t = torch.empty((ein.shape[0], 2, s.n, s.n), dtype=torch.float32, device=dev)
+            corr.pack(ec, dnc if s.c_in == 3 else None, s.dn_scale, x, targets=torch.stack(planes[1:]), t=t)
             xs.append(x)
-            ts.append(_to_channels(torch.stack(planes[1:])))
+            ts.append(t)
         assert B.bpm_check(fine) == 0 and B.bpm_check(coarse) == 0, B.bpm_last_error()
     finally:
         B.bpm_free(fine)
         B.bpm_free(coarse)
     return torch.cat(xs), torch.cat(ts)
+
+
+def residual_scale(corr: "B.Corrector", X, T, batch: int = 16) -> float:
+    """RMS size of the corrections over the training pairs, measured with the
+    network's own loss kernel while its last layer is still zero (f = 0)."""
+    total, count = 0.0, 0
+    for k in range(0, X.shape[0], batch):
+        xb, tb = X[k:k + batch], T[k:k + batch]
+        total += corr.loss_grad(xb, tb) * xb.shape[0]
+        count += xb.shape[0]
+    return math.sqrt(total / count)
 
 
 def train(corr: "B.Corrector", X, T, steps: int, batch: int = 16, lr: float = 1e-3, seed: int = 0,

@@ -195,8 +195,8 @@ __global__ void corr_reduce(const float* __restrict__ partial, int tiles, int P,
   grad[i] = s;
 }
 
-// out = x[:, :2] + z4; r = out - target; dz4 = 2 r / n; per-block sum of r^2
-__global__ void corr_loss(const float* __restrict__ x, int cin, const float* __restrict__ z4,
+// out = x[:, :2] + sigma z4; r = out - target; dz4 = 2 sigma r / n; per-block sum of r^2
+__global__ void corr_loss(const float* __restrict__ x, int cin, const float* __restrict__ z4, float sigma,
                           const float* __restrict__ target, float* __restrict__ dz4, float* __restrict__ part,
                           int batch, int hw) {
   __shared__ float red[256];
@@ -204,9 +204,9 @@ __global__ void corr_loss(const float* __restrict__ x, int cin, const float* __r
   float s = 0.f;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const size_t b = i / (2 * (size_t)hw), rem = i % (2 * (size_t)hw);
-    const float out = x[b * cin * hw + rem] + z4[i];
+    const float out = fmaf(sigma, z4[i], x[b * cin * hw + rem]);
     const float r = out - target[i];
-    dz4[i] = 2.f * r / (float)n;
+    dz4[i] = 2.f * sigma * r / (float)n;
     s = fmaf(r, r, s);
   }
   red[threadIdx.x] = s;
@@ -231,13 +231,13 @@ __global__ void corr_sum(const float* __restrict__ part, int n, float scale, flo
   if (threadIdx.x == 0) out[0] = (float)(red[0] * scale);
 }
 
-// out[b][:2] = x[b][:2] + z4[b]
-__global__ void corr_residual(const float* __restrict__ x, int cin, const float* __restrict__ z4,
+// out[b][:2] = x[b][:2] + sigma z4[b]
+__global__ void corr_residual(const float* __restrict__ x, int cin, const float* __restrict__ z4, float sigma,
                               float* __restrict__ out, int batch, int hw) {
   const size_t n = (size_t)batch * 2 * hw;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const size_t b = i / (2 * (size_t)hw), rem = i % (2 * (size_t)hw);
-    out[i] = x[b * cin * hw + rem] + z4[i];
+    out[i] = fmaf(sigma, z4[i], x[b * cin * hw + rem]);
   }
 }
 
@@ -261,24 +261,53 @@ __global__ void corr_round_bf16(const float* __restrict__ master, float* __restr
   if (i < n) work[i] = __bfloat162float(__float2bfloat16_rn(master[i]));
 }
 
-// x[b] = [Re E, Im E, (scale * dn)] from complex64 fields and an optional FP16 index plane
-__global__ void corr_pack(const float2* __restrict__ field, const __half* __restrict__ dn, float scale,
-                          float* __restrict__ x, int cin, int batch, int hw) {
-  const size_t n = (size_t)batch * hw;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t b = i / hw, p = i % hw;
-    const float2 e = field[i];
-    x[(b * cin + 0) * hw + p] = e.x;
-    x[(b * cin + 1) * hw + p] = e.y;
-    if (cin > 2) x[(b * cin + 2) * hw + p] = dn ? scale * __half2float(dn[i]) : 0.f;
+// Per-field RMS amplitude a[b] = sqrt(mean |E|^2) (FP64 accumulation), one
+// CTA per field; a field of zeros gets a = 1.
+__global__ void corr_field_rms(const float2* __restrict__ field, int hw, float* __restrict__ amp) {
+  __shared__ double red[256];
+  const float2* f = field + (size_t)blockIdx.x * hw;
+  double s = 0.0;
+  for (int p = threadIdx.x; p < hw; p += 256) s += (double)f[p].x * f[p].x + (double)f[p].y * f[p].y;
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double a = sqrt(red[0] / hw);
+    amp[blockIdx.x] = a > 0.0 ? (float)a : 1.0f;
   }
 }
 
-__global__ void corr_unpack(const float* __restrict__ out, float2* __restrict__ field, int batch, int hw) {
+// x[b] = [Re E / a_b, Im E / a_b, (scale * dn)] and, when target fields are
+// given, t[b] = [Re T / a_b, Im T / a_b]: the network sees every field at unit
+// RMS amplitude, so the correction it predicts scales linearly with the field
+__global__ void corr_pack(const float2* __restrict__ field, const float2* __restrict__ tfield,
+                          const __half* __restrict__ dn, float scale, const float* __restrict__ amp,
+                          float* __restrict__ x, float* __restrict__ t, int cin, int batch, int hw) {
   const size_t n = (size_t)batch * hw;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const size_t b = i / hw, p = i % hw;
-    field[i] = make_float2(out[(b * 2 + 0) * hw + p], out[(b * 2 + 1) * hw + p]);
+    const float inv = 1.0f / amp[b];
+    const float2 e = field[i];
+    x[(b * cin + 0) * hw + p] = e.x * inv;
+    x[(b * cin + 1) * hw + p] = e.y * inv;
+    if (cin > 2) x[(b * cin + 2) * hw + p] = dn ? scale * __half2float(dn[i]) : 0.f;
+    if (tfield) {
+      const float2 q = tfield[i];
+      t[(b * 2 + 0) * hw + p] = q.x * inv;
+      t[(b * 2 + 1) * hw + p] = q.y * inv;
+    }
+  }
+}
+
+__global__ void corr_unpack(const float* __restrict__ out, const float* __restrict__ amp, float2* __restrict__ field,
+                            int batch, int hw) {
+  const size_t n = (size_t)batch * hw;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / hw, p = i % hw;
+    field[i] = make_float2(out[(b * 2 + 0) * hw + p] * amp[b], out[(b * 2 + 1) * hw + p] * amp[b]);
   }
 }
 
@@ -306,9 +335,10 @@ struct bpm_corrector_s {
   float *x = nullptr;              // packed input [B][cin][H][W] (apply path)
   float *z[4] = {}, *a[3] = {};    // pre-activations and activations
   float *d0 = nullptr, *d1 = nullptr;   // backpropagated gradients (ping-pong)
-  float *partial = nullptr, *lpart = nullptr, *loss = nullptr, *outbuf = nullptr;
+  float *partial = nullptr, *lpart = nullptr, *loss = nullptr, *outbuf = nullptr, *amp = nullptr;
   size_t partial_floats = 0;
   int step = 0;
+  float sigma = 1.0f;              // residual scale: out = x[:, :2] + sigma f(x)
 };
 
 namespace {
@@ -373,7 +403,7 @@ int loss_grad(bpm_corrector_s* c, const float* x, const float* target, int batch
   if (rc) return rc;
   const int hw = h * w;
   const int lblocks = 256;
-  corr_loss<<<lblocks, 256, 0, s>>>(x, c->cin, c->z[3], target, c->d0, c->lpart, batch, hw);
+  corr_loss<<<lblocks, 256, 0, s>>>(x, c->cin, c->z[3], c->sigma, target, c->d0, c->lpart, batch, hw);
   corr_sum<<<1, 256, 0, s>>>(c->lpart, lblocks, 1.0f / (float)((size_t)batch * 2 * hw), c->loss);
   dim3 grid(w / kTile, h / kTile, batch);
   const int tiles = (w / kTile) * (h / kTile) * batch;
@@ -449,6 +479,7 @@ extern "C" int bpm_corrector_create(bpm_corrector_t* out, int in_channels, int m
   alloc(&c->lpart, 256);
   alloc(&c->loss, 1);
   alloc(&c->outbuf, (size_t)max_batch * 2 * max_h * max_w);
+  alloc(&c->amp, (size_t)max_batch);
   if (!ok) {
     cudaGetLastError();
     bpm_corrector_free(c);
@@ -467,6 +498,12 @@ extern "C" int bpm_corrector_create(bpm_corrector_t* out, int in_channels, int m
 }
 
 extern "C" int bpm_corrector_param_count(bpm_corrector_t c) { return c ? c->P : BPM_ERR_ARG; }
+
+extern "C" int bpm_corrector_set_residual_scale(bpm_corrector_t c, float sigma) {
+  if (!c || !(sigma > 0) || !std::isfinite(sigma)) return cfail(BPM_ERR_ARG, "sigma must be positive and finite");
+  c->sigma = sigma;
+  return BPM_OK;
+}
 
 extern "C" int bpm_corrector_set_params(bpm_corrector_t c, const float* h_params, int n, cudaStream_t stream) {
   if (!c || !h_params || n != c->P) return cfail(BPM_ERR_ARG, "need the corrector and %d parameters", c ? c->P : 0);
@@ -495,7 +532,8 @@ extern "C" int bpm_corrector_forward(bpm_corrector_t c, const float* d_x, float*
   if (rc) return rc;
   rc = forward(c, d_x, batch, h, w, stream);
   if (rc) return rc;
-  corr_residual<<<grid_for((size_t)batch * 2 * h * w), 256, 0, stream>>>(d_x, c->cin, c->z[3], d_out, batch, h * w);
+  corr_residual<<<grid_for((size_t)batch * 2 * h * w), 256, 0, stream>>>(d_x, c->cin, c->z[3], c->sigma, d_out,
+                                                                         batch, h * w);
   CORR_CU(cudaGetLastError());
   return BPM_OK;
 }
@@ -532,13 +570,15 @@ extern "C" int bpm_corrector_train_step(bpm_corrector_t c, const float* d_x, con
   return bpm_corrector_adam(c, lr, stream);
 }
 
-extern "C" int bpm_corrector_pack(bpm_corrector_t c, const void* d_fields, const void* d_dn, float dn_scale,
-                                  float* d_x, int batch, int h, int w, cudaStream_t stream) {
-  if (!c || !d_fields || !d_x) return cfail(BPM_ERR_ARG, "NULL argument");
-  if (batch < 1 || h < 1 || w < 1) return cfail(BPM_ERR_ARG, "bad sizes");
-  corr_pack<<<grid_for((size_t)batch * h * w), 256, 0, stream>>>(static_cast<const float2*>(d_fields),
-                                                                  static_cast<const __half*>(d_dn), dn_scale, d_x,
-                                                                  c->cin, batch, h * w);
+extern "C" int bpm_corrector_pack(bpm_corrector_t c, const void* d_fields, const void* d_targets, const void* d_dn,
+                                  float dn_scale, float* d_x, float* d_t, int batch, int h, int w,
+                                  cudaStream_t stream) {
+  if (!c || !d_fields || !d_x || (d_targets && !d_t)) return cfail(BPM_ERR_ARG, "NULL argument");
+  if (batch < 1 || batch > c->maxb || h < 1 || w < 1) return cfail(BPM_ERR_ARG, "bad sizes (batch <= %d)", c->maxb);
+  corr_field_rms<<<batch, 256, 0, stream>>>(static_cast<const float2*>(d_fields), h * w, c->amp);
+  corr_pack<<<grid_for((size_t)batch * h * w), 256, 0, stream>>>(
+      static_cast<const float2*>(d_fields), static_cast<const float2*>(d_targets), static_cast<const __half*>(d_dn),
+      dn_scale, c->amp, d_x, d_t, c->cin, batch, h * w);
   CORR_CU(cudaGetLastError());
   return BPM_OK;
 }
@@ -548,13 +588,16 @@ extern "C" int bpm_corrector_apply(bpm_corrector_t c, void* d_field, const void*
   if (!c || !d_field) return cfail(BPM_ERR_ARG, "NULL argument");
   int rc = check_dims(c, 1, h, w);
   if (rc) return rc;
-  corr_pack<<<grid_for((size_t)h * w), 256, 0, stream>>>(static_cast<const float2*>(d_field),
-                                                          static_cast<const __half*>(d_dn), dn_scale, c->x, c->cin,
-                                                          1, h * w);
+  corr_field_rms<<<1, 256, 0, stream>>>(static_cast<const float2*>(d_field), h * w, c->amp);
+  corr_pack<<<grid_for((size_t)h * w), 256, 0, stream>>>(static_cast<const float2*>(d_field), nullptr,
+                                                          static_cast<const __half*>(d_dn), dn_scale, c->amp, c->x,
+                                                          nullptr, c->cin, 1, h * w);
   rc = forward(c, c->x, 1, h, w, stream);
   if (rc) return rc;
-  corr_residual<<<grid_for((size_t)2 * h * w), 256, 0, stream>>>(c->x, c->cin, c->z[3], c->outbuf, 1, h * w);
-  corr_unpack<<<grid_for((size_t)h * w), 256, 0, stream>>>(c->outbuf, static_cast<float2*>(d_field), 1, h * w);
+  corr_residual<<<grid_for((size_t)2 * h * w), 256, 0, stream>>>(c->x, c->cin, c->z[3], c->sigma, c->outbuf, 1,
+                                                                  h * w);
+  corr_unpack<<<grid_for((size_t)h * w), 256, 0, stream>>>(c->outbuf, c->amp, static_cast<float2*>(d_field), 1,
+                                                            h * w);
   CORR_CU(cudaGetLastError());
   return BPM_OK;
 }
@@ -574,7 +617,7 @@ extern "C" int bpm_coarsen_index(const void* d_dn, int nz, int ny, int nx, int f
 extern "C" int bpm_corrector_free(bpm_corrector_t c) {
   if (!c) return BPM_OK;
   float* bufs[] = {c->master, c->work, c->m, c->v, c->grad, c->x, c->z[0], c->z[1], c->z[2], c->z[3],
-                   c->a[0], c->a[1], c->a[2], c->d0, c->d1, c->partial, c->lpart, c->loss, c->outbuf};
+                   c->a[0], c->a[1], c->a[2], c->d0, c->d1, c->partial, c->lpart, c->loss, c->outbuf, c->amp};
   for (float* b : bufs) cudaFree(b);
   delete c;
   return BPM_OK;

@@ -34,18 +34,20 @@ def test_forward_loss_and_gradients_match_oracle(B, c_in):
     X = rng.standard_normal((bsz, c_in, h, w)).astype(np.float32)
     T = rng.standard_normal((bsz, 2, h, w)).astype(np.float32)
     corr = B.Corrector(c_in, 4, 64, 64)
+    sigma = 0.37
     try:
+        corr.set_residual_scale(sigma)
         corr.set_params(theta.astype(np.float32))
         work = corr.get_params(which=1).astype(np.float64)        # BF16-rounded weights used by the kernels
         assert np.max(np.abs(work - theta)) <= 0.01 * np.max(np.abs(theta))
         xd, td = torch.from_numpy(X).to(dev), torch.from_numpy(T).to(dev)
         out = torch.empty((bsz, 2, h, w), dtype=torch.float32, device=dev)
         corr.forward(xd, out)
-        ref_out, _, _ = oc.forward(work, X.astype(np.float64))
+        ref_out, _, _ = oc.forward(work, X.astype(np.float64), sigma)
         assert rel(out.cpu().numpy(), ref_out) <= 1e-5
         loss = corr.loss_grad(xd, td)
         g = corr.get_params(which=2).astype(np.float64)
-        ref_loss, ref_g = oc.loss_and_grad(work, X.astype(np.float64), T.astype(np.float64))
+        ref_loss, ref_g = oc.loss_and_grad(work, X.astype(np.float64), T.astype(np.float64), sigma)
         assert loss == pytest.approx(ref_loss, rel=1e-5)
         k = 0
         for o, i in oc.layer_shapes(c_in):       # every layer's weights and biases
@@ -91,21 +93,28 @@ def test_coarsen_index(B):
     assert np.max(np.abs(got - ref)) <= 2 ** -11 * 0.05      # within FP16 rounding at |dn| <= 0.05
 
 
-def test_training_gains_over_coarse_steps_on_held_out_seeds(B):
+@pytest.mark.parametrize("c_in,min_gain", [(2, 1.05), (3, 1.5)])
+def test_training_gains_over_coarse_steps_on_held_out_seeds(B, c_in, min_gain):
+    """Train on pairs from seeds 4000-4047 (128^2 x 64 fine slices, 16 coarse
+    steps each); on held-out seeds 5000-5005 the field after the volume, coarse
+    steps with the corrector versus without, both against fine-step BPM.  The
+    2-channel network is the specified one; the 3-channel one also sees the
+    averaged index step."""
     from paper_1706_02261_b300 import corrector as C
     dev = torch.device("cuda")
-    s = C.Setup(n=128, nz=64, c_in=3)
+    s = C.Setup(n=128, nz=64, c_in=c_in)
     corr = B.Corrector(s.c_in, 16, s.n, s.n)
     try:
         corr.set_params(inputs.corrector_init(s.c_in, 0).astype(np.float32))
-        X, T = C.make_pairs(s, range(4000, 4024), corr, dev)
-        losses = C.train(corr, X, T, steps=600, batch=16, lr=1e-3, seed=1, log_every=50)
-        first = np.mean([l for _, l in losses[:2]])
-        last = np.mean([l for _, l in losses[-2:]])
-        assert last < 0.7 * first, losses
-        ev = C.evaluate(s, [5000, 5001, 5002], corr, dev)
+        X, T = C.make_pairs(s, range(4000, 4048), corr, dev)
+        sigma = C.residual_scale(corr, X, T)
+        corr.set_residual_scale(sigma)
+        losses = C.train(corr, X, T, steps=3000, batch=16, lr=1e-3, seed=1, log_every=500)
+        if c_in == 3:
+            assert losses[-1][1] < 0.5 * losses[0][1], losses
+        ev = C.evaluate(s, range(5000, 5006), corr, dev)
         gain = np.mean([r["coarse"] for r in ev]) / np.mean([r["corrected"] for r in ev])
-        print("held-out errors", ev, "gain", gain)
-        assert gain > 1.0, ev
+        print(f"c_in={c_in} sigma={sigma:.3e} losses={losses} held-out={ev} gain={gain:.2f}")
+        assert gain > min_gain, ev
     finally:
         corr.free()

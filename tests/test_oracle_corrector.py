@@ -52,7 +52,8 @@ def test_network_gradient_matches_finite_differences(c_in):
     theta += 0.05 * rng.standard_normal(theta.size)
     X = rng.standard_normal((2, c_in, 6, 5))
     T = rng.standard_normal((2, 2, 6, 5))
-    loss, g = oc.loss_and_grad(theta, X, T)
+    sigma = 0.3
+    loss, g = oc.loss_and_grad(theta, X, T, sigma)
     idx = rng.choice(theta.size, size=120, replace=False)
     h = 1e-6
     for k in idx:
@@ -60,7 +61,7 @@ def test_network_gradient_matches_finite_differences(c_in):
         tp[k] += h
         tm = theta.copy()
         tm[k] -= h
-        fd = (oc.loss_and_grad(tp, X, T)[0] - oc.loss_and_grad(tm, X, T)[0]) / (2 * h)
+        fd = (oc.loss_and_grad(tp, X, T, sigma)[0] - oc.loss_and_grad(tm, X, T, sigma)[0]) / (2 * h)
         assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])) + 1e-8, (k, fd, g[k])
 
 
