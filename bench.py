@@ -31,6 +31,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -47,9 +49,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["multiplex1024", "batch64"], default="multiplex1024",
+    ap.add_argument("--workload", choices=["multiplex1024", "batch64", "corrector512"], default="multiplex1024",
                     help="multiplex1024: the headline 1024^3 multiplexed-PSF field (default); "
-                         "batch64: 64 seeded instances of mixed sizes in one launch")
+                         "batch64: 64 seeded instances of mixed sizes in one launch; "
+                         "corrector512: 512^3 coarse steps with the learned corrector vs fine-step BPM")
     ap.add_argument("--nz", type=int, default=1024, help="slices (default: the full 1024)")
     ap.add_argument("--cpu-slices", type=int, default=32, help="slices in the oracle's timed sample")
     ap.add_argument("--no-e2e", action="store_true")
@@ -432,12 +435,91 @@ def run_batch(args):
     return 0
 
 
+def run_corrector(args):
+    """512^3, lambda 0.5 um, n0 1.33, light-sheet phantom recipe: fine-step BPM
+    (dz 0.1 um, 512 slices) against 128 coarse steps (dz 0.4 um) with and
+    without the learned corrector, trained first on pairs the propagation
+    generates (128^2 x 64-slice fields, seeds 4000+)."""
+    import torch
+    from paper_1706_02261_b300 import build as build_mod
+    from paper_1706_02261_b300 import inputs
+    build_mod.build()
+    from paper_1706_02261_b300 import bpm as B
+    from paper_1706_02261_b300 import corrector as C
+
+    dev = torch.device("cuda", 0)
+    res = {}
+    for c_in in (2, 3):
+        st = C.Setup(n=128, nz=64, c_in=c_in)
+        corr = B.Corrector(c_in, 16, 512, 512)
+        corr.set_params(inputs.corrector_init(c_in, 0).astype(np.float32))
+        t0 = time.perf_counter()
+        X, T = C.make_pairs(st, range(4000, 4080), corr, dev)
+        gen_s = time.perf_counter() - t0
+        corr.set_residual_scale(C.residual_scale(corr, X, T))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        C.train(corr, X, T, steps=4000, batch=16, lr=1e-3, seed=1)
+        torch.cuda.synchronize(dev)
+        train_s = time.perf_counter() - t0
+        big = C.Setup(n=512, nz=512, c_in=c_in)
+        fine = B.bpm_plan(B.Instance(512, 512, 0.1, 0.1))
+        coarse = B.bpm_plan(B.Instance(512, 128, 0.1, 0.4))
+        rows = []
+        for seed in (5000, 5001, 5002):
+            dn = torch.from_numpy(inputs.sphere_phantom_dn((512, 512, 512), 0.1, big.spheres(), seed)).to(dev)
+            dnc = torch.empty((128, 512, 512), dtype=torch.float16, device=dev)
+            B.bpm_coarsen_index(dn, 4, dnc)
+            E0 = C.input_field(big, seed, fine, dev)
+            ef, ec, e = torch.empty_like(E0), E0.clone(), E0.clone()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+            ev[0].record()
+            B.bpm_propagate(fine, dn, E0, ef, None)
+            ev[1].record()
+            ev[2].record()
+            B.bpm_propagate(coarse, dnc, ec, ec, None)
+            ev[3].record()
+            ev[4].record()
+            for j in range(128):
+                B.bpm_propagate(coarse, dnc, e, e, None, j, j + 1)
+                corr.apply(e, dnc[j] if c_in == 3 else None, big.dn_scale)
+            ev[5].record()
+            torch.cuda.synchronize(dev)
+            nrm = torch.linalg.vector_norm(ef)
+            rows.append({"seed": seed, "fine_ms": ev[0].elapsed_time(ev[1]), "coarse_ms": ev[2].elapsed_time(ev[3]),
+                         "corrected_ms": ev[4].elapsed_time(ev[5]),
+                         "coarse_err": float(torch.linalg.vector_norm(ec - ef) / nrm),
+                         "corrected_err": float(torch.linalg.vector_norm(e - ef) / nrm)})
+        B.bpm_free(fine)
+        B.bpm_free(coarse)
+        corr.free()
+        res[f"c_in={c_in}"] = {"pairs": int(X.shape[0]), "pair_generation_s": gen_s, "train_s": train_s,
+                               "train_steps": 4000, "held_out_512": rows,
+                               "mean_err_coarse": float(np.mean([r["coarse_err"] for r in rows])),
+                               "mean_err_corrected": float(np.mean([r["corrected_err"] for r in rows]))}
+    r2 = res["c_in=2"]["held_out_512"]
+    t_corr = statistics.mean(r["corrected_ms"] for r in r2) / 1e3
+    line = {"metric": "fine-equivalent voxel-steps/s of 512^3 coarse steps with the learned corrector",
+            "value": 512.0 ** 3 / t_corr, "unit": UNIT, "n_gpus": 1, "steps": 3, "warmup": 0,
+            "ms_per_step": t_corr * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (BF16 weights)", "data": "synthetic",
+            "config": {"workload": "corrector512: 512^3, dz 0.1 um fine / 0.4 um coarse, light-sheet phantom recipe, "
+                                   "held-out seeds 5000-5002"},
+            "fine_bpm_ms": statistics.mean(r["fine_ms"] for r in r2),
+            "coarse_bpm_ms": statistics.mean(r["coarse_ms"] for r in r2),
+            "results": res, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "corrector512":
+        return run_corrector(args)
     return run_ours(args)
 
 
