@@ -153,24 +153,40 @@ template <> struct Cfg<1024> : LoopCfg<1024, 32, 32, 32, 1058> {};
 // exp(i x) for the phase screen.  For |x| <= pi/4 (|dn| <= 0.38 at the
 // paper's wavelengths and slice thicknesses) the Taylor series of sin and cos
 // truncated after x^11 and x^12 (truncation below 1e-11) is evaluated by
-// Horner's rule in x^2; larger arguments use sincosf.
-__device__ __forceinline__ float2 unit_phasor(float x) {
-  float s, c;
-  if (fabsf(x) <= 0.785398163f) {
-    const float x2 = x * x;
-    const float ps = fmaf(fmaf(fmaf(fmaf(x2, -2.50521084e-8f, 2.75573192e-6f), x2, -1.98412698e-4f), x2,
-                               8.33333333e-3f),
-                          x2, -1.66666667e-1f);
-    s = fmaf(ps, x2 * x, x);
-    c = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(x2, 2.08767570e-9f, -2.75573192e-7f), x2, 2.48015873e-5f), x2,
-                            -1.38888889e-3f),
-                       x2, 4.16666667e-2f),
-                  x2, -0.5f),
-             x2, 1.0f);
-  } else {
-    sincosf(x, &s, &c);
-  }
+// Horner's rule in x^2 (branch free); larger arguments use sincosf.  Callers
+// pick the evaluation once per warp (phasor_small_range) so that the loop
+// over a row's elements has no per-element branch and its independent
+// elements can interleave.
+constexpr float kPhasorPolyMax = 0.785398163f;
+
+__device__ __forceinline__ float2 unit_phasor_poly(float x) {
+  const float x2 = x * x;
+  const float ps = fmaf(fmaf(fmaf(fmaf(x2, -2.50521084e-8f, 2.75573192e-6f), x2, -1.98412698e-4f), x2,
+                             8.33333333e-3f),
+                        x2, -1.66666667e-1f);
+  const float s = fmaf(ps, x2 * x, x);
+  const float c = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(x2, 2.08767570e-9f, -2.75573192e-7f), x2, 2.48015873e-5f), x2,
+                                      -1.38888889e-3f),
+                                 x2, 4.16666667e-2f),
+                            x2, -0.5f),
+                       x2, 1.0f);
   return make_float2(c, s);
+}
+
+__device__ __forceinline__ float2 unit_phasor_libm(float x) {
+  float s, c;
+  sincosf(x, &s, &c);
+  return make_float2(c, s);
+}
+
+__device__ __forceinline__ float2 unit_phasor(float x) {
+  return fabsf(x) <= kPhasorPolyMax ? unit_phasor_poly(x) : unit_phasor_libm(x);
+}
+
+// true when every lane's largest |screen phase| allows the polynomial
+// (NaN index values keep the polynomial; they are reported separately)
+__device__ __forceinline__ bool phasor_small_range(float max_abs_phase) {
+  return __all_sync(0xffffffffu, !(max_abs_phase > kPhasorPolyMax));
 }
 
 // Everything one propagation (or synthesis) launch needs.
@@ -390,21 +406,36 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
       if (active && a.inten)
         irow = st.inten ? st.inten + (size_t)(row - r0) * N : a.inten + ((size_t)z * N + row) * N;
       const bool i_smem = st.inten != nullptr;
-      // phase screen exp(i k0 dn dz) and |E|^2 on the natural-order field
+      // phase screen exp(i k0 dn dz) and |E|^2 on the natural-order field;
+      // the evaluation of the phasor (polynomial or sincosf) is chosen once per
+      // warp so the element loop is branch free and its elements interleave
       auto screen = [&](float2* w) {
+        // index values of this thread's elements: from the shared-memory rows
+        // (prefetched) or the registers fetched before the transform
+        float dval[C::PTS];
+        float mx = 0.f;
 #pragma unroll
         for (int q = 0; q < C::PTS; ++q) {
-          const int x = layout_index<N, C::T, C::R0>(q, t);
-          const float d = __half2float(sdn ? sdn[x] : dv[q]);
-          bad |= active && !isfinite(d);
-          const float2 e = cmul(w[q], unit_phasor(a.screen_c * d));
-          w[q] = e;
-          if (irow) {
-            const float iv = fmaf(e.x, e.x, e.y * e.y);
-            if (i_smem) irow[x] = iv;
-            else __stcs(irow + x, iv);
-          }
+          dval[q] = __half2float(sdn ? sdn[layout_index<N, C::T, C::R0>(q, t)] : dv[q]);
+          mx = fmaxf(mx, fabsf(dval[q]));
         }
+        const bool poly = phasor_small_range(a.screen_c * mx);
+        auto body = [&](auto phasor) {
+#pragma unroll
+          for (int q = 0; q < C::PTS; ++q) {
+            const int x = layout_index<N, C::T, C::R0>(q, t);
+            bad |= active && !isfinite(dval[q]);
+            const float2 e = cmul(w[q], phasor(a.screen_c * dval[q]));
+            w[q] = e;
+            if (irow) {
+              const float iv = fmaf(e.x, e.x, e.y * e.y);
+              if (i_smem) irow[x] = iv;
+              else __stcs(irow + x, iv);
+            }
+          }
+        };
+        if (poly) body([](float ph) { return unit_phasor_poly(ph); });
+        else body([](float ph) { return unit_phasor_libm(ph); });
       };
       if constexpr (MODE == ROW_LAST) {
         C::inv(v, buf, s_twf, s_twi, t);
@@ -470,10 +501,12 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
       const float2* hcol = st.h ? st.h + (size_t)((active ? col : c0) - c0) * N
                                 : a.ht + (size_t)(active ? col : c0) * N;
       C::fwd_mid_inv(v, buf, s_twf, s_twi, t, [&](float2* w) {
+        if (st.h) {
 #pragma unroll
-        for (int q = 0; q < C::PTS; ++q) {
-          const int ky = layout_index<N, C::T, C::RL>(q, t);
-          w[q] = cmul(w[q], st.h ? hcol[ky] : __ldg(hcol + ky));
+          for (int q = 0; q < C::PTS; ++q) w[q] = cmul(w[q], hcol[layout_index<N, C::T, C::RL>(q, t)]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < C::PTS; ++q) w[q] = cmul(w[q], __ldg(hcol + layout_index<N, C::T, C::RL>(q, t)));
         }
       });
     } else {
