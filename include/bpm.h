@@ -140,6 +140,27 @@ int bpm_propagate(bpm_plan_t p, const void *const *d_dn, const void *const *d_Ei
 int bpm_propagate_static(const bpm_instance_desc *inst, const void *d_dn, const void *d_Ein,
                          void *d_Eout, float *d_I, int z_begin, int z_end, cudaStream_t stream);
 
+/* bpm_propagate_host - bpm_propagate of all nz slices of a single-instance
+ * plan with HOST index and intensity volumes: the library streams the FP16
+ * index volume to the device and the intensity volume back in chunks of
+ * `chunk` slices through two device ring slots, so that the host->device
+ * copies, the propagation (one persistent launch per chunk, the field staying
+ * on the device) and the device->host copies overlap on three streams.
+ *   h_dn   : host [nz][ny][nx] FP16 index volume
+ *   Ein    : input field, host memory (ein_on_device = 0) or device memory
+ *            (ein_on_device = 1, e.g. from bpm_multiplex_psf)
+ *   h_Eout : host [ny][nx] complex float, receives the field after the volume
+ *   h_I    : NULL or host [nz][ny][nx] float, receives |E|^2 per slice
+ * Host buffers should be page-locked (cudaHostAlloc/cudaHostRegister; torch's
+ * pin_memory) for the copies to overlap; pageable buffers work but serialise.
+ * The plan owns the ring (2 * chunk * nx * ny * 6 bytes, allocated on the
+ * first call or when a larger chunk is requested).  Synchronous: returns when
+ * h_Eout and h_I are complete, with the device status (as bpm_check).
+ * Errors: BPM_ERR_ARG, BPM_ERR_ALIGN, BPM_ERR_UNSUPPORTED (batched plans),
+ * BPM_ERR_CUDA, BPM_ERR_TIMEOUT, BPM_ERR_NAN. */
+int bpm_propagate_host(bpm_plan_t p, const void *h_dn, const void *Ein, int ein_on_device, void *h_Eout,
+                       float *h_I, int chunk, cudaStream_t stream);
+
 /* bpm_multiplex_psf - the multiplexed input field of the method paragraph:
  * the sum of n_foci focused fields, one per emitter.  Emitter j sits at the
  * grid point nearest to (h_xyz[3j], h_xyz[3j+1]) (rounded in FP64 as

@@ -63,9 +63,10 @@ _lib.bpm_last_error.restype = ctypes.c_char_p
 _lib.bpm_plan_info.argtypes = [_vp, ctypes.POINTER(_i), _i]
 _lib.bpm_debug_set_barrier_timeout.argtypes = [_vp, ctypes.c_ulonglong, _u]
 _lib.bpm_autotune.argtypes = [_vp, _pp, _pp, _pp, _pp, _i, _vp]
+_lib.bpm_propagate_host.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _i, _vp]
 _lib.bpm_propagate_static.argtypes = [ctypes.POINTER(bpm_instance_desc), _vp, _vp, _vp, _vp, _i, _i, _vp]
 for _f in ("bpm_plan", "bpm_propagate", "bpm_multiplex_psf", "bpm_light_sheet", "bpm_check",
-           "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout", "bpm_propagate_static", "bpm_autotune"):
+           "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout", "bpm_propagate_static", "bpm_autotune", "bpm_propagate_host"):
     getattr(_lib, _f).restype = _i
 
 
@@ -146,6 +147,20 @@ def bpm_propagate(plan, dn, e_in, e_out, inten=None, z_begin: int = 0, z_end: in
     a_out = _arr([_ptr(t) for t in e_out])
     a_i = _arr([_ptr(t) if t is not None else ctypes.c_void_p(0) for t in inten]) if inten is not None else None
     return _check(_lib.bpm_propagate(plan, a_dn, a_in, a_out, a_i, z_begin, z_end, _stream_handle(stream)))
+
+
+def bpm_propagate_host(plan, dn_host, e_in, e_out_host, inten_host=None, chunk: int = 64, stream=None) -> int:
+    """Whole propagation with host index/intensity volumes (pinned torch CPU
+    tensors or numpy arrays); e_in may be a host or a CUDA tensor."""
+    def hp(t):
+        if t is None:
+            return None
+        if isinstance(t, np.ndarray):
+            return ctypes.c_void_p(t.ctypes.data)
+        return ctypes.c_void_p(t.data_ptr())
+    on_dev = int(hasattr(e_in, "is_cuda") and e_in.is_cuda)
+    return _check(_lib.bpm_propagate_host(plan, hp(dn_host), hp(e_in), on_dev, hp(e_out_host), hp(inten_host),
+                                          chunk, _stream_handle(stream)))
 
 
 def bpm_autotune(plan, dn, e_in, e_out, inten=None, z_probe: int = 8, stream=None) -> int:

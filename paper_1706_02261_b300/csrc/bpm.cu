@@ -144,6 +144,14 @@ struct bpm_plan_s {
   bool have_args = false;           // h_inst holds the arguments of the last call
   cudaStream_t cap = nullptr;       // capture stream for BPM_FLAG_GRAPH
   cudaGraphExec_t gexec = nullptr;
+  // host-buffer streaming (bpm_propagate_host): two-slot rings of index and
+  // intensity chunks, the field, copy streams and events (created on first use)
+  int host_chunk = 0;
+  __half* ring_dn[2] = {nullptr, nullptr};
+  float* ring_i[2] = {nullptr, nullptr};
+  float2* host_field = nullptr;
+  cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+  cudaEvent_t ev_h2d[2] = {}, ev_prop[2] = {}, ev_d2h[2] = {};
 };
 
 namespace {
@@ -237,6 +245,16 @@ void free_plan(bpm_plan_s* p) {
   if (p->h_inst) cudaFreeHost(p->h_inst);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->cap) cudaStreamDestroy(p->cap);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(p->ring_dn[k]);
+    cudaFree(p->ring_i[k]);
+    if (p->ev_h2d[k]) cudaEventDestroy(p->ev_h2d[k]);
+    if (p->ev_prop[k]) cudaEventDestroy(p->ev_prop[k]);
+    if (p->ev_d2h[k]) cudaEventDestroy(p->ev_d2h[k]);
+  }
+  cudaFree(p->host_field);
+  if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
+  if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
   delete p;
 }
 
@@ -715,6 +733,81 @@ extern "C" int bpm_plan_info(bpm_plan_t p, int* out, int n_out) {
   }
   for (int i = 0; i < n_out && i < 5; ++i) out[i] = vals[i];
   return BPM_OK;
+}
+
+extern "C" int bpm_propagate_host(bpm_plan_t p, const void* h_dn, const void* Ein, int ein_on_device, void* h_Eout,
+                                  float* h_I, int chunk, cudaStream_t stream) {
+  if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
+  if (p->inst.size() != 1) return fail(BPM_ERR_UNSUPPORTED, "bpm_propagate_host takes single-instance plans");
+  if (!h_dn || !Ein || !h_Eout) return fail(BPM_ERR_ARG, "h_dn, Ein and h_Eout must be non-NULL");
+  if (chunk < 1) return fail(BPM_ERR_ARG, "chunk must be >= 1");
+  if (ein_on_device && !aligned16(Ein)) return fail(BPM_ERR_ALIGN, "device Ein must be 16-byte aligned");
+  const InstPlan& in = p->inst[0];
+  const int nz = in.d.nz;
+  const size_t M = (size_t)in.d.nx * in.d.ny;
+  chunk = std::min(chunk, std::max(nz, 1));
+  if (chunk > p->host_chunk) {
+    BPM_CU(cudaStreamSynchronize(p->last));
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(p->ring_dn[k]);
+      cudaFree(p->ring_i[k]);
+      p->ring_dn[k] = nullptr;
+      p->ring_i[k] = nullptr;
+    }
+    p->host_chunk = 0;
+    for (int k = 0; k < 2; ++k) {
+      BPM_CU(cudaMalloc(&p->ring_dn[k], (size_t)chunk * M * sizeof(__half)));
+      BPM_CU(cudaMalloc(&p->ring_i[k], (size_t)chunk * M * sizeof(float)));
+    }
+    p->host_chunk = chunk;
+  }
+  if (!p->host_field) BPM_CU(cudaMalloc(&p->host_field, M * sizeof(float2)));
+  if (!p->s_h2d) BPM_CU(cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking));
+  if (!p->s_d2h) BPM_CU(cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking));
+  for (int k = 0; k < 2; ++k) {
+    if (!p->ev_h2d[k]) BPM_CU(cudaEventCreateWithFlags(&p->ev_h2d[k], cudaEventDisableTiming));
+    if (!p->ev_prop[k]) BPM_CU(cudaEventCreateWithFlags(&p->ev_prop[k], cudaEventDisableTiming));
+    if (!p->ev_d2h[k]) BPM_CU(cudaEventCreateWithFlags(&p->ev_d2h[k], cudaEventDisableTiming));
+  }
+  // the field enters once; chunks then stream through the two ring slots:
+  //   copy-in stream : index chunk k -> slot k%2 (after the propagation of chunk k-2 freed it)
+  //   stream         : propagation of chunk k (after its index arrived and the
+  //                    intensity slot was drained by chunk k-2's copy-out)
+  //   copy-out stream: intensity chunk k -> host (after the propagation of chunk k)
+  BPM_CU(cudaMemcpyAsync(p->host_field, Ein, M * sizeof(float2),
+                         ein_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
+  const __half* hdn = static_cast<const __half*>(h_dn);
+  const int nchunks = (nz + chunk - 1) / chunk;
+  for (int k = 0; k < nchunks; ++k) {
+    const int slot = k & 1, z0 = k * chunk, c = std::min(chunk, nz - z0);
+    if (k >= 2) BPM_CU(cudaStreamWaitEvent(p->s_h2d, p->ev_prop[slot], 0));
+    BPM_CU(cudaMemcpyAsync(p->ring_dn[slot], hdn + (size_t)z0 * M, (size_t)c * M * sizeof(__half),
+                           cudaMemcpyHostToDevice, p->s_h2d));
+    BPM_CU(cudaEventRecord(p->ev_h2d[slot], p->s_h2d));
+    BPM_CU(cudaStreamWaitEvent(stream, p->ev_h2d[slot], 0));
+    if (k >= 2 && h_I) BPM_CU(cudaStreamWaitEvent(stream, p->ev_d2h[slot], 0));
+    const void* dn_arr[1] = {p->ring_dn[slot]};
+    const void* ein_arr[1] = {p->host_field};
+    void* eout_arr[1] = {p->host_field};
+    float* i_arr[1] = {h_I ? p->ring_i[slot] : nullptr};
+    const unsigned keep = p->flags;
+    p->flags &= ~(unsigned)BPM_FLAG_SYNC;
+    int rc = bpm_propagate(p, dn_arr, ein_arr, eout_arr, i_arr, 0, c, stream);
+    p->flags = keep;
+    if (rc) return rc;
+    BPM_CU(cudaEventRecord(p->ev_prop[slot], stream));
+    if (h_I) {
+      BPM_CU(cudaStreamWaitEvent(p->s_d2h, p->ev_prop[slot], 0));
+      BPM_CU(cudaMemcpyAsync(h_I + (size_t)z0 * M, p->ring_i[slot], (size_t)c * M * sizeof(float),
+                             cudaMemcpyDeviceToHost, p->s_d2h));
+      BPM_CU(cudaEventRecord(p->ev_d2h[slot], p->s_d2h));
+    }
+  }
+  BPM_CU(cudaMemcpyAsync(h_Eout, p->host_field, M * sizeof(float2), cudaMemcpyDeviceToHost, stream));
+  BPM_CU(cudaStreamSynchronize(p->s_h2d));
+  BPM_CU(cudaStreamSynchronize(p->s_d2h));
+  p->last = stream;
+  return bpm_check(p);
 }
 
 extern "C" int bpm_autotune(bpm_plan_t p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
