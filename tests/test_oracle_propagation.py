@@ -126,3 +126,23 @@ def test_gaussian_beam_matches_angular_spectrum_quadrature():
         # I[z] is recorded after slice z, i.e. at depth (z + 1) dz
         ref_mid = _hankel_gaussian(rho, 10 * dz, w0)
         assert abs(I[9, n // 2 + oy, n // 2 + ox] - abs(ref_mid) ** 2) < 1e-9
+
+
+def test_screen_acts_after_diffraction_within_a_slice():
+    """Step order: each slice diffracts first, then applies its screen.  A
+    phase screen present only in the last slice is then a pure phase on the
+    final field, so the last intensity slice equals that of the homogeneous
+    run pointwise; applied before the diffraction it would change it."""
+    n, dx, dz, nz, w0 = 64, 0.1, 0.1, 6, 1.0
+    x = (np.arange(n) - n // 2) * dx
+    E0 = np.exp(-(x[None, :] ** 2 + x[:, None] ** 2) / w0 ** 2)
+    dn = np.zeros((nz, n, n))
+    dn[-1] = 0.5 * (np.sin(2 * np.pi * x / 0.8)[None, :] > 0)          # strong binary grating
+    _, Ih = oracle.bpm(np.zeros((nz, n, n)), E0, dx, dx, dz, LAM, N0)
+    _, Ig = oracle.bpm(dn, E0, dx, dx, dz, LAM, N0)
+    assert np.max(np.abs(Ig[-1] - Ih[-1])) < 1e-12 * np.max(Ih[-1])
+    # and the grating does change the slices after it when it is not last
+    dn2 = np.zeros((nz, n, n))
+    dn2[-2] = dn[-1]
+    _, Ig2 = oracle.bpm(dn2, E0, dx, dx, dz, LAM, N0)
+    assert np.max(np.abs(Ig2[-1] - Ih[-1])) > 1e-3 * np.max(Ih[-1])
