@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--cpu-slices", type=int, default=32, help="slices in the oracle's timed sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT slice-loop comparison")
     return ap.parse_args()
 
 
@@ -197,6 +198,46 @@ def run_reference(args):
     return 0
 
 
+def cufft_slice_loop(w, dn_d, e0, eout_ours, stream):
+    """Comparison only: the same split-step through torch.fft (cuFFT) and
+    torch pointwise kernels, one slice at a time, timed once over the whole
+    depth with the intensity volume written.  Not part of the product path."""
+    import torch
+    n, nz = w.n, dn_d.shape[0]
+    dev = dn_d.device
+    k0 = 2 * math.pi / w.lam
+    K = k0 * w.n0
+    k = 2 * math.pi * np.fft.fftfreq(n, w.d)
+    kz2 = K * K - k[None, :] ** 2 - k[:, None] ** 2
+    H = np.where(kz2 > 0, np.exp(1j * np.sqrt(np.maximum(kz2, 0)) * w.d), 0)
+    Hd = torch.from_numpy(H.astype(np.complex64)).to(dev)
+    inten = torch.empty((nz, n, n), dtype=torch.float32, device=dev)
+    scale = k0 * w.d
+
+    def volume(zn):
+        e = e0.clone()
+        for z in range(zn):
+            e = torch.fft.ifft2(torch.fft.fft2(e) * Hd)
+            phase = dn_d[z].float() * scale
+            e = e * torch.polar(torch.ones_like(phase), phase)
+            inten[z] = e.real * e.real + e.imag * e.imag
+        return e
+
+    with torch.cuda.stream(stream):
+        volume(8)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        e = volume(nz)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+    t = a.elapsed_time(b) / 1e3
+    err = float(torch.linalg.vector_norm(e - eout_ours) / torch.linalg.vector_norm(eout_ours))
+    return {"ms_per_volume": t * 1e3, "value": float(n) * n * nz / t, "unit": UNIT,
+            "kind": "torch.fft (cuFFT) fft2/ifft2 + torch pointwise per slice, eager, FP32",
+            "field_rel_l2_vs_ours": err}
+
+
 def _kernel_hash() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -329,6 +370,10 @@ def run_ours(args):
                 "hbm_achieved_gbs": step_bytes(n, nz) / kern_s / 1e9, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac_of_measured": step_bytes(n, nz) / kern_s / 1e9 / hbm_peak}
 
+    cufft = None
+    if not args.no_cufft:
+        cufft = cufft_slice_loop(w, dn_d, e0, eout, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(w, dn16, foci, args.cpu_slices)
@@ -344,7 +389,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (2 GiB index volume, 4 GiB intensity volume per step)",
                        "team_ctas": info["team_ctas"], "plan_ms": plan_ms},
             "roofline": roofline, "clocks": clocks.summary(), "gpu_launches": launches_per_step * args.steps,
-            "e2e": e2e, "cpu_baseline": cpu}
+            "e2e": e2e, "cpu_baseline": cpu, "cufft_comparison": cufft}
     if rank == 0:
         print(json.dumps(line), flush=True)
     B.bpm_free(plan)

@@ -1,0 +1,118 @@
+"""Parity at the workloads' full sizes, in the launch configuration the
+benchmark times (one plan, default flags, the whole depth in one
+bpm_propagate call).
+
+* 256^3 light sheet through the 300-sphere phantom: the oracle runs the whole
+  volume, so every output is compared.
+* 1024^3 multiplexed PSFs through the 800-sphere phantom: the oracle computes
+  the first 16 intensity planes of the same run.  At every depth, the
+  properties that hold for any grid are checked: the screen is unitary and the
+  cut propagator can only remove power, so the slice energy never grows (and
+  stays constant for a field inside the propagating band), and the output
+  field's modulus squared is the last intensity plane.
+* 1024^3 multiplexed PSFs through a homogeneous medium: the exact propagator
+  composes (H(dz)^k = H(k dz)), so the oracle's single step over k dz gives
+  the planes at any depth, here the field after all 1024 slices and sampled
+  intensity planes.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1706_02261_b300 import inputs  # noqa: E402
+from tests.gpu_util import FIELD_TOL, INTENSITY_TOL, field_rel_l2, intensity_rel_max  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1706_02261_b300 import bpm
+    return bpm
+
+
+def test_light_sheet_256_whole_volume(B):
+    w = inputs.light_sheet_256()
+    dn16 = w.dn()
+    dev = torch.device("cuda")
+    plan = B.bpm_plan(B.Instance(w.n, w.nz, w.d, w.d, w.lam, w.n0))
+    try:
+        e0 = torch.empty((w.n, w.n), dtype=torch.complex64, device=dev)
+        B.bpm_light_sheet(plan, 0, w.sheet_NA, w.sheet_zf(), e0)
+        eout = torch.empty_like(e0)
+        I = torch.empty((w.nz, w.n, w.n), dtype=torch.float32, device=dev)
+        B.bpm_propagate(plan, torch.from_numpy(dn16).to(dev), e0, eout, I)
+        assert B.bpm_check(plan) == B.BPM_OK, B.bpm_last_error()
+        Eg, Ig = eout.cpu().numpy(), I.cpu().numpy()
+    finally:
+        B.bpm_free(plan)
+    E0 = oracle.light_sheet(w.n, w.n, w.d, w.d, w.lam, w.n0, w.sheet_NA, w.sheet_zf())
+    Er, Ir = oracle.bpm(inputs.dn_to_f64(dn16), E0, w.d, w.d, w.d, w.lam, w.n0)
+    ef, ei = field_rel_l2(Eg, Er), intensity_rel_max(Ig, Ir)
+    print(f"256^3 light sheet: field rel L2 {ef:.2e}, intensity max rel {ei:.2e}")
+    assert ef <= FIELD_TOL
+    assert ei <= INTENSITY_TOL
+
+
+def _run_1024(B, dn16, w, f):
+    dev = torch.device("cuda")
+    plan = B.bpm_plan(B.Instance(w.n, w.nz, w.d, w.d, w.lam, w.n0))
+    try:
+        e0 = torch.empty((w.n, w.n), dtype=torch.complex64, device=dev)
+        B.bpm_multiplex_psf(plan, 0, f.xyz_um(w.d, w.d), f.phase, f.NA, e0)
+        eout = torch.empty_like(e0)
+        I = torch.empty((w.nz, w.n, w.n), dtype=torch.float32, device=dev)
+        dn_d = torch.from_numpy(dn16).to(dev)
+        B.bpm_propagate(plan, dn_d, e0, eout, I)
+        assert B.bpm_check(plan) == B.BPM_OK, B.bpm_last_error()
+        del dn_d
+        energy = I.to(torch.float64).sum(dim=(1, 2)).cpu().numpy()
+        e_out = eout.cpu().numpy()
+        return e_out, I, energy
+    finally:
+        B.bpm_free(plan)
+
+
+def test_multiplex_1024_cubed_phantom(B):
+    w = inputs.multiplex_1024(nz=1024)
+    dn16 = w.dn()
+    f = w.foci()
+    Eg, I, energy = _run_1024(B, dn16, w, f)
+    k = 16
+    E0 = oracle.multiplex_psf(w.n, w.n, w.d, w.d, w.lam, w.n0, f.ix, f.iy, f.phase, f.zf, f.NA)
+    _, Ir = oracle.bpm(inputs.dn_to_f64(dn16[:k]), E0, w.d, w.d, w.d, w.lam, w.n0)
+    ei = intensity_rel_max(I[:k].cpu().numpy(), Ir)
+    # energy: never grows beyond FP32 rounding; the foci's spectrum lies inside
+    # NA 0.6 < n0, so almost nothing is cut either
+    e_in = float(np.sum(np.abs(E0) ** 2))
+    growth = float(np.max(np.diff(energy)) / e_in)
+    drift = float(np.max(np.abs(energy - e_in)) / e_in)
+    last = float(np.max(np.abs(np.abs(Eg) ** 2 - I[-1].cpu().numpy())) / I[-1].max().item())
+    print(f"1024^3 phantom: first {k} planes intensity max rel {ei:.2e}; energy growth {growth:.1e}, "
+          f"drift {drift:.1e}; |E_out|^2 vs last plane {last:.1e}")
+    assert ei <= INTENSITY_TOL
+    assert growth <= 1e-5
+    assert drift <= 1e-3
+    assert last <= 1e-5
+    assert np.all(np.isfinite(Eg))
+
+
+def test_multiplex_1024_cubed_homogeneous_against_single_exact_step(B):
+    w = inputs.multiplex_1024(nz=1024)
+    f = w.foci()
+    dn16 = np.zeros((w.nz, w.n, w.n), np.float16)
+    Eg, I, _ = _run_1024(B, dn16, w, f)
+    E0 = oracle.multiplex_psf(w.n, w.n, w.d, w.d, w.lam, w.n0, f.ix, f.iy, f.phase, f.zf, f.NA)
+    zero = np.zeros((1, w.n, w.n))
+    Er, _ = oracle.bpm(zero, E0, w.d, w.d, w.nz * w.d, w.lam, w.n0)
+    ef = field_rel_l2(Eg, Er)
+    errs = []
+    for z in (0, 127, 511):
+        _, Ir = oracle.bpm(zero, E0, w.d, w.d, (z + 1) * w.d, w.lam, w.n0)
+        errs.append(intensity_rel_max(I[z].cpu().numpy(), Ir[0]))
+    print(f"1024^3 homogeneous: field after 1024 slices rel L2 {ef:.2e}; intensity planes 1/128/512 {errs}")
+    assert ef <= FIELD_TOL
+    assert max(errs) <= INTENSITY_TOL
