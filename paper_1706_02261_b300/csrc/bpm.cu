@@ -98,6 +98,16 @@ std::vector<float2> twiddles_for() {
     append_twiddles(v, N, C::T, radix_list<typename C::F::Rad>(), -1);
     append_twiddles(v, N, C::T, radix_list<typename C::I::Rad>(), +1);
   }
+  if constexpr (C::TW4 > 0) {
+    // four-step column transform: W_N^(a k) at [k N1 + a], forward sign
+    const int N1 = C::FS_N1;
+    for (int k = 0; k < N1; ++k)
+      for (int a = 0; a < N1; ++a) {
+        const long long e = (long long)a * k % N;
+        const double ang = -kTwoPi * (double)e / (double)N;
+        v.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+      }
+  }
   return v;
 }
 
@@ -159,7 +169,7 @@ namespace {
 template <int N>
 int setup_kernels(NRes& r, int sms) {
   using C = Cfg<N>;
-  r.smem = C::smem_bytes();
+  r.smem = cfg_smem_bytes<C>();
   const int smem = (int)r.smem;
   BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -178,7 +188,7 @@ int setup_kernels(NRes& r, int sms) {
   BPM_CU(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
   r.rmax = (N + r.team - 1) / r.team;
   auto rup = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  const size_t hb = rup((size_t)r.rmax * N * sizeof(float2)), db = rup((size_t)r.rmax * N * 2),
+  const size_t hb = rup((size_t)r.rmax * C::HS * sizeof(float2)), db = rup((size_t)r.rmax * N * 2),
                ib = rup((size_t)r.rmax * N * sizeof(float));
   const size_t budget = (size_t)max_optin - 1024;   // static shared memory of the kernel
   r.h_res = r.dn_stage = r.i_stage = 1;
@@ -193,7 +203,7 @@ int setup_kernels(NRes& r, int sms) {
                                                        r.smem_persist));
   if (per_sm < 1) return fail(BPM_ERR_UNSUPPORTED, "persistent kernel for N=%d does not fit on an SM", N);
   std::vector<float2> tw = twiddles_for<N>();
-  if (tw.size() != (size_t)(C::TWF + C::TWI) || tw.empty())
+  if (tw.size() != (size_t)cfg_twiddles<C>() || tw.empty())
     return fail(BPM_ERR_UNSUPPORTED, "twiddle table size mismatch for N=%d", N);
   BPM_CU(cudaMalloc(&r.tw, tw.size() * sizeof(float2)));
   BPM_CU(cudaMemcpy(r.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
@@ -936,7 +946,7 @@ template <int N>
 int static_propagate(const bpm_instance_desc& d, unsigned char* scratch, const void* d_dn, const void* d_Ein,
                      void* d_Eout, float* d_I, int zb, int ze, cudaStream_t stream) {
   using C = Cfg<N>;
-  static_assert(C::TWF + C::TWI <= (int)kStaticTwiddleFloat2, "twiddle region too small");
+  static_assert(cfg_twiddles<C>() <= (int)kStaticTwiddleFloat2 && C::TW4 == 0, "twiddle region too small");
   // launch configuration: the same rule as a plan's (setup_kernels)
   int sms = 0, dev = 0, max_optin = 0;
   BPM_CU(cudaGetDevice(&dev));
@@ -944,11 +954,11 @@ int static_propagate(const bpm_instance_desc& d, unsigned char* scratch, const v
   BPM_CU(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   NRes r;
   r.n = N;
-  r.smem = C::smem_bytes();
+  r.smem = cfg_smem_bytes<C>();
   r.team = std::max(1, std::min((N + C::NG - 1) / C::NG, sms));
   r.rmax = (N + r.team - 1) / r.team;
   auto rup = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  const size_t hb = rup((size_t)r.rmax * N * sizeof(float2)), db = rup((size_t)r.rmax * N * 2),
+  const size_t hb = rup((size_t)r.rmax * C::HS * sizeof(float2)), db = rup((size_t)r.rmax * N * 2),
                ib = rup((size_t)r.rmax * N * sizeof(float));
   const size_t budget = (size_t)max_optin - 1024;
   r.h_res = r.dn_stage = r.i_stage = 1;

@@ -49,6 +49,10 @@ struct CfgBase {
   static constexpr int PTS = N_ / T_;
   static constexpr int GPW = 32 / T_;
   static constexpr int NG = kWarps * GPW;   // row/column groups per CTA
+  // four-step column transform (FourStepCfg): off by default
+  static constexpr int FS_N1 = 0, FS_SA = 0, FS_SC = 0, TW4 = 0;
+  static constexpr int BUFLEN = NG * GS_;   // float2 of the group / exchange buffers
+  static constexpr int HS = N_;             // row stride of the staged propagator columns
 };
 
 template <int N_, int T_, int R_, int PAD_, int GS_>
@@ -93,9 +97,6 @@ struct LoopCfg : CfgBase<N_, T_, GS_> {
     }
     conj_all(v, E::PTS);
   }
-  static constexpr size_t smem_bytes() {
-    return sizeof(float2) * (size_t)(TWF + TWI + CfgBase<N_, T_, GS_>::NG * GS_);
-  }
 };
 
 template <int N_, int T_, int GS_, class F_, class I_>
@@ -128,9 +129,31 @@ struct GroupCfg : CfgBase<N_, T_, GS_> {
     mid(v);
     I::run(v, buf, twi, t);
   }
-  static constexpr size_t smem_bytes() {
-    return sizeof(float2) * (size_t)(TWF + TWI + CfgBase<N_, T_, GS_>::NG * GS_);
-  }
+};
+
+// Columns of N = N1 * N1 points as a four-step transform (N1 threads per
+// column, NG = kThreads / N1 columns per round): thread (a, c), a =
+// threadIdx / NG and c = threadIdx % NG, holds y = a + N1 b of column c in
+// v[b].  A forward transform is an N1-point DFT over b in registers, the
+// twiddle W_N^(a k), an exchange through shared memory (row a of column c's
+// N1 x N1 block written, column a read), and a second N1-point DFT; its
+// output X[a + N1 k] is in v[k], the same layout as the input, so the
+// propagator multiply and the inverse (by conjugation) follow in registers.
+// Global loads and stores go straight to registers: per warp instruction,
+// rows a .. a + 32/NG - 1 of NG adjacent columns (64-byte segments at
+// N1 = 32).  Strides: a row of the block SA = 1 (mod 16) float2 and a column
+// block SC = 32 / NG (mod 16), so that both the row writes and the column
+// reads of a warp fall on distinct bank pairs; the staged propagator columns
+// use the row stride HS = N + 32 / NG for the same reason.
+template <class Base, int N1>
+struct FourStepCfg : Base {
+  static_assert(N1 * N1 == Base::N && N1 * Base::NG == kThreads, "four-step layout needs N = N1^2, N1 NG = kThreads");
+  static constexpr int FS_N1 = N1;
+  static constexpr int FS_SA = (N1 + 15) / 16 * 16 + 1;
+  static constexpr int FS_SC = N1 * FS_SA + ((32 / Base::NG) % 16 - (N1 * FS_SA) % 16 + 16) % 16;
+  static constexpr int TW4 = Base::N;       // W_N^(a k) at [k N1 + a]
+  static constexpr int BUFLEN = Base::NG * FS_SC > Base::NG * Base::GS ? Base::NG * FS_SC : Base::NG * Base::GS;
+  static constexpr int HS = Base::N + 32 / Base::NG;
 };
 
 using Rad8x16 = Radices<8, 16>;
@@ -148,15 +171,26 @@ template <> struct Cfg<192> : GroupCfg<192, 8, 219, GroupFFT<192, 8, 8, -1, Rad8
 template <> struct Cfg<256> : LoopCfg<256, 16, 16, 16, 273> {};
 template <> struct Cfg<384> : GroupCfg<384, 16, 409, GroupFFT<384, 16, 16, -1, Rad8x8x6>, GroupFFT<384, 16, 16, +1, Rad6x8x8>> {};
 template <> struct Cfg<512> : LoopCfg<512, 16, 8, 16, 545> {};
-template <> struct Cfg<1024> : LoopCfg<1024, 32, 32, 32, 1058> {};
+template <> struct Cfg<1024> : FourStepCfg<LoopCfg<1024, 32, 32, 32, 1058>, 32> {};
 
-// exp(i x) for the phase screen.  For |x| <= pi/4 (|dn| <= 0.38 at the
+// shared memory of the half-step kernels: twiddle tables, then the buffers
+template <class C>
+__host__ __device__ constexpr size_t cfg_smem_bytes() {
+  return sizeof(float2) * (size_t)(C::TWF + C::TWI + C::TW4 + C::BUFLEN);
+}
+template <class C>
+__host__ __device__ constexpr int cfg_twiddles() {
+  return C::TWF + C::TWI + C::TW4;
+}
+
+// exp(i x) for the phase screen.  For |x| <= 1/4 (|dn| <= 0.12 at the
 // paper's wavelengths and slice thicknesses) the Taylor series of sin and cos
-// truncated after x^11 and x^12 (truncation below 1e-11) is evaluated by
-// Horner's rule in x^2 (branch free); larger arguments use sincosf.  Callers
-// pick the evaluation once per warp (phasor_small_range) so that the loop
-// over a row's elements has no per-element branch and its independent
-// elements can interleave.
+// truncated after x^7 and x^8 (truncation below 1.1e-11), for |x| <= pi/4
+// after x^11 and x^12 (truncation below 1e-11), both evaluated by Horner's
+// rule in x^2 (branch free); larger arguments use sincosf.  Callers pick the
+// evaluation once per warp (phasor_range) so that the loop over a row's
+// elements has no per-element branch and its independent elements can
+// interleave.
 constexpr float kPhasorPolyMax = 0.785398163f;
 
 __device__ __forceinline__ float2 unit_phasor_poly(float x) {
@@ -173,20 +207,29 @@ __device__ __forceinline__ float2 unit_phasor_poly(float x) {
   return make_float2(c, s);
 }
 
+constexpr float kPhasorSmallMax = 0.25f;
+
+__device__ __forceinline__ float2 unit_phasor_small(float x) {
+  const float x2 = x * x;
+  const float ps = fmaf(fmaf(x2, -1.98412698e-4f, 8.33333333e-3f), x2, -1.66666667e-1f);
+  const float s = fmaf(ps, x2 * x, x);
+  const float c =
+      fmaf(fmaf(fmaf(fmaf(x2, 2.48015873e-5f, -1.38888889e-3f), x2, 4.16666667e-2f), x2, -0.5f), x2, 1.0f);
+  return make_float2(c, s);
+}
+
 __device__ __forceinline__ float2 unit_phasor_libm(float x) {
   float s, c;
   sincosf(x, &s, &c);
   return make_float2(c, s);
 }
 
-__device__ __forceinline__ float2 unit_phasor(float x) {
-  return fabsf(x) <= kPhasorPolyMax ? unit_phasor_poly(x) : unit_phasor_libm(x);
-}
-
-// true when every lane's largest |screen phase| allows the polynomial
-// (NaN index values keep the polynomial; they are reported separately)
-__device__ __forceinline__ bool phasor_small_range(float max_abs_phase) {
-  return __all_sync(0xffffffffu, !(max_abs_phase > kPhasorPolyMax));
+// The evaluation every lane of the warp can use, from each lane's largest
+// |screen phase|: 0 the short polynomial, 1 the long one, 2 sincosf (NaN
+// index values keep a polynomial; they are reported separately).
+__device__ __forceinline__ int phasor_range(float max_abs_phase) {
+  if (__all_sync(0xffffffffu, !(max_abs_phase > kPhasorSmallMax))) return 0;
+  return __all_sync(0xffffffffu, !(max_abs_phase > kPhasorPolyMax)) ? 1 : 2;
 }
 
 // Everything one propagation (or synthesis) launch needs.
@@ -336,15 +379,23 @@ __device__ __forceinline__ bool team_barrier(const StepArgs& a, unsigned& epoch,
 enum RowMode { ROW_FWD = 0, ROW_STEP = 1, ROW_LAST = 2, ROW_INV_ACC = 3 };
 enum ColMode { COL_PROP = 0, COL_FOCUS = 1 };
 
+// Loads in the order the first radix-R pass consumes them, stores in the
+// order the last one produces them (dft_input_order / dft_output_order).
 template <int N, int T, int R>
 __device__ __forceinline__ void load_layout(float2* v, const float2* __restrict__ src, int t) {
 #pragma unroll
-  for (int k = 0; k < N / T; ++k) v[k] = __ldcg(src + layout_index<N, T, R>(k, t));
+  for (int i = 0; i < N / T; ++i) {
+    const int k = (i / R) * R + dft_input_order<R>(i % R);
+    v[k] = __ldcg(src + layout_index<N, T, R>(k, t));
+  }
 }
 template <int N, int T, int R>
 __device__ __forceinline__ void store_layout(const float2* v, float2* dst, int t) {
 #pragma unroll
-  for (int k = 0; k < N / T; ++k) __stcg(dst + layout_index<N, T, R>(k, t), v[k]);
+  for (int i = 0; i < N / T; ++i) {
+    const int k = (i / R) * R + dft_output_order<R>(i % R);
+    __stcg(dst + layout_index<N, T, R>(k, t), v[k]);
+  }
 }
 
 // Rows [r0, r1) of the team member; each group of T threads takes one row per
@@ -413,18 +464,19 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
         // index values of this thread's elements: from the shared-memory rows
         // (prefetched) or the registers fetched before the transform
         float dval[C::PTS];
-        float mx = 0.f;
+        float mx = 0.f, sum = 0.f;    // fmaxf skips NaN; the sum keeps NaN and inf
 #pragma unroll
         for (int q = 0; q < C::PTS; ++q) {
           dval[q] = __half2float(sdn ? sdn[layout_index<N, C::T, C::R0>(q, t)] : dv[q]);
           mx = fmaxf(mx, fabsf(dval[q]));
+          sum += dval[q];
         }
-        const bool poly = phasor_small_range(a.screen_c * mx);
+        bad |= active && !isfinite(sum);
+        const int range = phasor_range(a.screen_c * mx);
         auto body = [&](auto phasor) {
 #pragma unroll
           for (int q = 0; q < C::PTS; ++q) {
             const int x = layout_index<N, C::T, C::R0>(q, t);
-            bad |= active && !isfinite(dval[q]);
             const float2 e = cmul(w[q], phasor(a.screen_c * dval[q]));
             w[q] = e;
             if (irow) {
@@ -434,7 +486,8 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
             }
           }
         };
-        if (poly) body([](float ph) { return unit_phasor_poly(ph); });
+        if (range == 0) body([](float ph) { return unit_phasor_small(ph); });
+        else if (range == 1) body([](float ph) { return unit_phasor_poly(ph); });
         else body([](float ph) { return unit_phasor_libm(ph); });
       };
       if constexpr (MODE == ROW_LAST) {
@@ -453,14 +506,87 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
   }
 }
 
+// One forward four-step transform of the columns held as in FourStepCfg:
+// N1-point DFT over the registers, twiddles W_N^(a k) (tw = table + a, read
+// with stride N1: the NG threads of a row share each value), exchange
+// (xw: this thread's row of its column block, xr: its column, stride SA),
+// N1-point DFT.  Two CTA barriers: the buffer is free before it is written,
+// and complete before it is read.
+template <int N1, int SA>
+__device__ __forceinline__ void four_step_fwd(float2* v, const float2* tw, float2* xw, const float2* xr) {
+  Dft<N1, -1>::run(v);
+#pragma unroll
+  for (int k = 1; k < N1; ++k) v[k] = cmul(v[k], tw[k * N1]);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < N1; ++k) xw[k] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < N1; ++j) v[j] = xr[j * SA];
+  Dft<N1, -1>::run(v);
+}
+
+// Columns [c0, c1) by four-step transforms (FourStepCfg): load, FFT_y,
+// propagator H^T[col][ky], inverse FFT_y (conjugated forward), store, NG
+// columns per round, all in registers apart from the two exchanges.
+template <int N>
+__device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int c1, float2* s_buf,
+                                                 const float2* s_tw4, const Stage& st) {
+  using C = Cfg<N>;
+  constexpr int N1 = C::FS_N1, NG = C::NG, SA = C::FS_SA, SC = C::FS_SC;
+  const int c = threadIdx.x % NG, ai = threadIdx.x / NG;
+  const float2* tw = s_tw4 + ai;
+  float2* xw = s_buf + c * SC + ai * SA;
+  const float2* xr = s_buf + c * SC + ai;
+  for (int cb = c0; cb < c1; cb += NG) {
+    const int col = cb + c;
+    const bool on = col < c1;
+    float2 v[N1];
+    {
+      const float2* src = a.work + (on ? col : c0);
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        const int b = dft_input_order<N1>(i);
+        v[b] = __ldcg(src + (size_t)(ai + N1 * b) * N);
+      }
+    }
+    four_step_fwd<N1, SA>(v, tw, xw, xr);
+    if (st.h) {
+      const float2* h = st.h + (size_t)((on ? col : c0) - c0) * C::HS + ai;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) v[k] = cmul(v[k], h[N1 * k]);
+    } else {
+      const float2* h = a.ht + (size_t)(on ? col : c0) * N + ai;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) v[k] = cmul(v[k], __ldg(h + N1 * k));
+    }
+    conj_all(v, N1);
+    four_step_fwd<N1, SA>(v, tw, xw, xr);
+    conj_all(v, N1);
+    if (on) {
+      float2* dst = a.work + col;
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        const int b = dft_output_order<N1>(i);
+        __stcg(dst + (size_t)(ai + N1 * b) * N, v[b]);
+      }
+    }
+  }
+}
+
 // Columns [c0, c1) of the team member, NG columns per round staged in shared
 // memory (column g of the round at s_buf + g * GS, index padded like the
-// forward transform's exchange buffer).
+// forward transform's exchange buffer).  Sizes with a four-step layout take
+// col_half_step_4s for the propagator.
 template <int N, int MODE>
 __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1, float2* s_buf,
                                               const float2* s_twf, const float2* s_twi,
                                               const Stage& st = Stage()) {
   using C = Cfg<N>;
+  if constexpr (C::FS_N1 > 0 && MODE == COL_PROP) {
+    col_half_step_4s<N>(a, c0, c1, s_buf, s_twi + C::TWI, st);
+    return;
+  }
   const int lane = threadIdx.x & 31;
   const int gid = (threadIdx.x >> 5) * C::GPW + lane / C::T;
   const int t = lane % C::T;
@@ -498,7 +624,7 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
       v[q] = active ? buf[C::f(layout_index<N, C::T, C::R0>(q, t))] : make_float2(0.f, 0.f);
     __syncwarp();
     if constexpr (MODE == COL_PROP) {
-      const float2* hcol = st.h ? st.h + (size_t)((active ? col : c0) - c0) * N
+      const float2* hcol = st.h ? st.h + (size_t)((active ? col : c0) - c0) * C::HS
                                 : a.ht + (size_t)(active ? col : c0) * N;
       C::fwd_mid_inv(v, buf, s_twf, s_twi, t, [&](float2* w) {
         if (st.h) {
@@ -557,12 +683,9 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
 
 template <int N>
 __device__ __forceinline__ void load_twiddles(const StepArgs& a, float2* s_twf, float2* s_twi) {
-  using C = Cfg<N>;
-  for (int i = threadIdx.x; i < C::TWF + C::TWI; i += kThreads) {
-    float2 w = __ldg(a.tw + i);
-    if (i < C::TWF) s_twf[i] = w;
-    else s_twi[i - C::TWF] = w;
-  }
+  // the tables are contiguous: forward, inverse, four-step
+  (void)s_twi;
+  for (int i = threadIdx.x; i < cfg_twiddles<Cfg<N>>(); i += kThreads) s_twf[i] = __ldg(a.tw + i);
   __syncthreads();
 }
 
@@ -587,8 +710,8 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
   float2* s_twi = s_twf + C::TWF;
-  float2* s_buf = s_twi + C::TWI;
-  char* s_extra = reinterpret_cast<char*>(s_buf + C::NG * C::GS);
+  float2* s_buf = s_twi + C::TWI + C::TW4;
+  char* s_extra = reinterpret_cast<char*>(s_buf + C::BUFLEN);
   __shared__ int s_flag;
   __shared__ __align__(8) uint64_t s_mbar;
   const int G = gridDim.x, rank = blockIdx.x;
@@ -599,7 +722,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
     size_t off = 0;
     if (a.h_res) {
       st.h = reinterpret_cast<const float2*>(s_extra + off);
-      off += ((size_t)a.rmax * N * sizeof(float2) + 15) & ~(size_t)15;
+      off += ((size_t)a.rmax * C::HS * sizeof(float2) + 15) & ~(size_t)15;
     }
     if (a.dn_stage) {
       st.dn = reinterpret_cast<const __half*>(s_extra + off);
@@ -610,7 +733,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
   if (a.h_res) {
     float2* dst = const_cast<float2*>(st.h);
     const float2* src = a.ht + (size_t)lo * N;
-    for (int i = threadIdx.x; i < nrow * N; i += kThreads) dst[i] = __ldg(src + i);
+    for (int i = threadIdx.x; i < nrow * N; i += kThreads) dst[(i / N) * C::HS + i % N] = __ldg(src + i);
   }
   if (threadIdx.x == 0 && a.dn_stage) mbar_init(&s_mbar, 1);
   load_twiddles<N>(a, s_twf, s_twi);    // ends with __syncthreads
@@ -662,7 +785,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_row_kernel(StepArgs a, int z)
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
   float2* s_twi = s_twf + C::TWF;
-  float2* s_buf = s_twi + C::TWI;
+  float2* s_buf = s_twi + C::TWI + C::TW4;
   load_twiddles<N>(a, s_twf, s_twi);
   const int G = gridDim.x, rank = blockIdx.x;
   const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
@@ -677,7 +800,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_col_kernel(StepArgs a) {
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
   float2* s_twi = s_twf + C::TWF;
-  float2* s_buf = s_twi + C::TWI;
+  float2* s_buf = s_twi + C::TWI + C::TW4;
   load_twiddles<N>(a, s_twf, s_twi);
   const int G = gridDim.x, rank = blockIdx.x;
   const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
@@ -694,8 +817,8 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_light_sheet_kernel(StepArgs a
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
   float2* s_twi = s_twf + C::TWF;
-  float2* s_buf = s_twi + C::TWI;
-  float2* line = s_buf + C::NG * C::GS;
+  float2* s_buf = s_twi + C::TWI + C::TW4;
+  float2* line = s_buf + C::BUFLEN;
   __shared__ double s_part[kThreads];
   load_twiddles<N>(a, s_twf, s_twi);
   const double nd = __dmul_rn((double)N, a.dx);
@@ -871,7 +994,7 @@ __device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int
   using C = Cfg<N>;
   float2* s_twf = smem;
   float2* s_twi = s_twf + C::TWF;
-  float2* s_buf = s_twi + C::TWI;
+  float2* s_buf = s_twi + C::TWI + C::TW4;
   StepArgs a;
   a.work = ia.work;
   a.ein = ia.ein;

@@ -194,6 +194,24 @@ struct Dft {
   }
 };
 
+// Order in which Dft<R> first consumes its inputs and last produces its
+// outputs: inputs by decimation subsequence (n1 + P n2, n1 outer), outputs by
+// final P-point DFT (k1 + M k2, k1 outer).  Loads issued in the first order
+// let the first inner DFTs start while later loads are still in flight;
+// stores issued in the second follow the values as they are finished.
+template <int R>
+__host__ __device__ constexpr int dft_input_order(int i) {
+  constexpr int P = (R % 4 == 0) ? 4 : ((R % 2 == 0) ? 2 : 3);
+  constexpr int M = R / P;
+  return (R <= 4 || P * M != R) ? i : P * (i % M) + i / M;
+}
+template <int R>
+__host__ __device__ constexpr int dft_output_order(int i) {
+  constexpr int P = (R % 4 == 0) ? 4 : ((R % 2 == 0) ? 2 : 3);
+  constexpr int M = R / P;
+  return (R <= 4 || P * M != R) ? i : i / P + M * (i % P);
+}
+
 // ---------------------------------------------------------------------------
 // group transform over shared memory (mixed radices, fully unrolled)
 // ---------------------------------------------------------------------------
