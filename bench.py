@@ -54,7 +54,7 @@ def parse_args():
                          "batch64: 64 seeded instances of mixed sizes in one launch; "
                          "corrector512: 512^3 coarse steps with the learned corrector vs fine-step BPM")
     ap.add_argument("--nz", type=int, default=1024, help="slices (default: the full 1024)")
-    ap.add_argument("--cpu-slices", type=int, default=32, help="slices in the oracle's timed sample")
+    ap.add_argument("--cpu-slices", type=int, default=128, help="slices in the oracle's timed sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT slice-loop comparison")

@@ -179,14 +179,18 @@ int setup_kernels(NRes& r, int sms) {
   BPM_CU(cudaFuncSetAttribute(bpm_col_kernel<N, COL_FOCUS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   BPM_CU(cudaFuncSetAttribute(bpm_light_sheet_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               smem + (int)(C::GS * sizeof(float2))));
-  // smallest team that gives every group one row per half-step, at most one CTA per SM
-  const int want = (N + C::NG - 1) / C::NG;
+  // smallest team that gives every group one row per half-step, at most one
+  // CTA per SM; with the four-step column layout every SM takes rows (fewer
+  // rows per CTA) while the columns stay in aligned groups of NG
+  const int want = C::FS_N1 > 0 ? N : (N + C::NG - 1) / C::NG;
   r.team = std::max(1, std::min(want, sms));
   // staging buffers of the persistent kernel, dropped (propagator columns
   // first) if they would not fit next to the group buffers
   int max_optin = 0;
   BPM_CU(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
+  // rows (and columns) per CTA at most: columns come in whole groups of NG
   r.rmax = (N + r.team - 1) / r.team;
+  r.rmax = (r.rmax + C::NG - 1) / C::NG * C::NG;
   auto rup = [](size_t b) { return (b + 15) & ~(size_t)15; };
   const size_t hb = rup((size_t)r.rmax * C::HS * sizeof(float2)), db = rup((size_t)r.rmax * N * 2),
                ib = rup((size_t)r.rmax * N * sizeof(float));

@@ -697,7 +697,8 @@ __device__ __forceinline__ void report_bad(const StepArgs& a, bool bad) {
 // kernels
 // ---------------------------------------------------------------------------
 
-// The whole slice loop in one cooperative launch; gridDim.x CTAs form the team.
+// The whole slice loop in one cooperative launch; gridDim.x CTAs form the team
+// (rows split evenly, columns in aligned groups of NG).
 // Shared memory: twiddles | group buffers | [propagator columns of this CTA]
 // | [index rows of the current slice] | [intensity rows of the current slice].
 // The index rows of slice z are fetched by one bulk copy issued when the
@@ -717,6 +718,11 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
   const int G = gridDim.x, rank = blockIdx.x;
   const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
   const int nrow = hi - lo;
+  // columns in whole groups of NG (aligned 64-byte segments at N = 1024): a
+  // team larger than N / NG leaves its last CTAs without columns, while every
+  // CTA still takes rows
+  const int cper = (N + G - 1) / G, CB = (cper + C::NG - 1) / C::NG * C::NG;
+  const int clo = min(N, rank * CB), chi = min(N, clo + CB);
   Stage st;
   {
     size_t off = 0;
@@ -732,8 +738,8 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
   }
   if (a.h_res) {
     float2* dst = const_cast<float2*>(st.h);
-    const float2* src = a.ht + (size_t)lo * N;
-    for (int i = threadIdx.x; i < nrow * N; i += kThreads) dst[(i / N) * C::HS + i % N] = __ldg(src + i);
+    const float2* src = a.ht + (size_t)clo * N;
+    for (int i = threadIdx.x; i < (chi - clo) * N; i += kThreads) dst[(i / N) * C::HS + i % N] = __ldg(src + i);
   }
   if (threadIdx.x == 0 && a.dn_stage) mbar_init(&s_mbar, 1);
   load_twiddles<N>(a, s_twf, s_twi);    // ends with __syncthreads
@@ -751,7 +757,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
       }
       dn_pending = true;
     }
-    col_half_step<N, COL_PROP>(a, lo, hi, s_buf, s_twf, s_twi, st);
+    col_half_step<N, COL_PROP>(a, clo, chi, s_buf, s_twf, s_twi, st);
     if (!team_barrier(a, epoch, &s_flag)) break;
     bool ok = true;
     if (dn_pending) {
