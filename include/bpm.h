@@ -111,6 +111,36 @@ int bpm_propagate(bpm_plan_t p, const void *const *d_dn, const void *const *d_Ei
                   void *const *d_Eout, float *const *d_I, int z_begin, int z_end,
                   cudaStream_t stream);
 
+/* bpm_propagate_window - bpm_propagate with an intensity window per
+ * instance: instance i computes |E|^2 only for slices z in
+ * [h_w_begin[i], h_w_end[i]) (and in [z_begin, z_end)), into d_I[i] laid out
+ * [h_w_end[i] - h_w_begin[i]][ny][nx] with slice z at offset
+ * (z - h_w_begin[i])*nx*ny.  This is how a PSF sweep writes only the slices
+ * around the foci (the paper's multiplexing scheme: each multiplexed field is
+ * needed near its focal depth only, and propagation can stop at the window's
+ * end by z_end).  bpm_propagate is this call with windows [0, nz_i).
+ *   h_w_begin, h_w_end : host arrays of n_inst ints, 0 <= w_begin <= w_end
+ * Other arguments and errors as bpm_propagate. */
+int bpm_propagate_window(bpm_plan_t p, const void *const *d_dn, const void *const *d_Ein,
+                         void *const *d_Eout, float *const *d_I, int z_begin, int z_end,
+                         const int *h_w_begin, const int *h_w_end, cudaStream_t stream);
+
+/* bpm_demultiplex - cut one patch per focus out of an intensity window, the
+ * de-multiplexing step of the paper's multiplexed PSF calculation (a set of
+ * non-overlapping PSFs computed in one propagation is split into the
+ * individual PSFs).  Patch j is
+ *   d_out[j][k][y][x] = I(iz_j - pz/2 + k, iy_j - py/2 + y, ix_j - px/2 + x)
+ * for k < pz, y < py, x < px, with lateral indices taken modulo the grid size
+ * (the periodic boundary of the propagation) and 0 for slices outside the
+ * window [w_begin, w_begin + w_nz).
+ *   inst     : instance whose grid (nx = ny) is used
+ *   d_I      : device float window [w_nz][ny][nx] (slice z at (z - w_begin)*nx*ny)
+ *   h_foci   : host array of n_foci (ix, iy, iz) voxel triples, 0 <= ix, iy < nx
+ *   d_out    : device float [n_foci][pz][py][px], written with streaming stores
+ * Errors: BPM_ERR_ARG (focus outside the grid, bad sizes, NULL), BPM_ERR_CUDA. */
+int bpm_demultiplex(bpm_plan_t p, int inst, const float *d_I, int w_begin, int w_nz, int n_foci,
+                    const int *h_foci, int px, int py, int pz, float *d_out, cudaStream_t stream);
+
 /* bpm_propagate_static - the same propagation as bpm_propagate for one
  * instance, for callers that cannot allocate device memory.  Some callers run
  * inside a host application whose allocator owns the whole device (cudaMalloc

@@ -65,6 +65,8 @@ _lib.bpm_debug_set_barrier_timeout.argtypes = [_vp, ctypes.c_ulonglong, _u]
 _lib.bpm_autotune.argtypes = [_vp, _pp, _pp, _pp, _pp, _i, _vp]
 _lib.bpm_propagate_host.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _i, _vp]
 _lib.bpm_propagate_static.argtypes = [ctypes.POINTER(bpm_instance_desc), _vp, _vp, _vp, _vp, _i, _i, _vp]
+_lib.bpm_propagate_window.argtypes = [_vp, _pp, _pp, _pp, _pp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), _vp]
+_lib.bpm_demultiplex.argtypes = [_vp, _i, _vp, _i, _i, _i, ctypes.POINTER(_i), _i, _i, _i, _vp, _vp]
 for _f in ("bpm_plan", "bpm_propagate", "bpm_multiplex_psf", "bpm_light_sheet", "bpm_check",
            "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout", "bpm_propagate_static", "bpm_autotune", "bpm_propagate_host"):
     getattr(_lib, _f).restype = _i
@@ -147,6 +149,36 @@ def bpm_propagate(plan, dn, e_in, e_out, inten=None, z_begin: int = 0, z_end: in
     a_out = _arr([_ptr(t) for t in e_out])
     a_i = _arr([_ptr(t) if t is not None else ctypes.c_void_p(0) for t in inten]) if inten is not None else None
     return _check(_lib.bpm_propagate(plan, a_dn, a_in, a_out, a_i, z_begin, z_end, _stream_handle(stream)))
+
+
+def bpm_propagate_window(plan, dn, e_in, e_out, inten, w_begin, w_end, z_begin: int = 0,
+                         z_end: int = 2 ** 31 - 1, stream=None) -> int:
+    """bpm_propagate writing |E|^2 only for slices [w_begin, w_end) of each
+    instance into inten (w_end - w_begin slices).  Single tensors or lists;
+    w_begin, w_end: ints or lists of ints (one per instance)."""
+    single = not isinstance(e_in, (list, tuple))
+    dn, e_in, e_out, inten = ([dn], [e_in], [e_out], [inten]) if single else (dn, e_in, e_out, inten)
+    wb = [w_begin] if single else list(w_begin)
+    we = [w_end] if single else list(w_end)
+    a_dn = _arr([_ptr(t) or ctypes.c_void_p(0) for t in dn])
+    a_in = _arr([_ptr(t) for t in e_in])
+    a_out = _arr([_ptr(t) for t in e_out])
+    a_i = _arr([_ptr(t) if t is not None else ctypes.c_void_p(0) for t in inten])
+    c_wb = (_i * len(wb))(*wb)
+    c_we = (_i * len(we))(*we)
+    return _check(_lib.bpm_propagate_window(plan, a_dn, a_in, a_out, a_i, z_begin, z_end, c_wb, c_we,
+                                            _stream_handle(stream)))
+
+
+def bpm_demultiplex(plan, inst: int, inten, w_begin: int, foci, patch, out, stream=None) -> int:
+    """Cut patch = (px, py, pz) around each focus (rows of foci: ix, iy, iz
+    voxel indices) out of the intensity window inten [w_nz][n][n] that starts
+    at slice w_begin; out: float tensor [n_foci][pz][py][px]."""
+    f = np.ascontiguousarray(np.asarray(foci, dtype=np.int32).reshape(-1, 3))
+    px, py, pz = patch
+    return _check(_lib.bpm_demultiplex(plan, inst, _ptr(inten), w_begin, int(inten.shape[0]), f.shape[0],
+                                       f.ctypes.data_as(ctypes.POINTER(_i)), px, py, pz, _ptr(out),
+                                       _stream_handle(stream)))
 
 
 def bpm_propagate_host(plan, dn_host, e_in, e_out_host, inten_host=None, chunk: int = 64, stream=None) -> int:

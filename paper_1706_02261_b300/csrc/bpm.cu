@@ -138,6 +138,8 @@ struct bpm_plan_s {
   int* err = nullptr;
   unsigned long long* npupil = nullptr;
   int* foci_idx = nullptr;
+  int* demux_foci = nullptr;        // bpm_demultiplex: device copy of the focus list
+  int demux_cap = 0;
   double* foci_phase = nullptr;
   int foci_cap = 0;
   unsigned long long timeout_ns = 2000000000ull;
@@ -251,6 +253,7 @@ void free_plan(bpm_plan_s* p) {
   cudaFree(p->err);
   cudaFree(p->npupil);
   cudaFree(p->foci_idx);
+  cudaFree(p->demux_foci);
   cudaFree(p->foci_phase);
   cudaFree(p->d_inst);
   cudaFree(p->d_order);
@@ -445,7 +448,8 @@ int enqueue_batch(bpm_plan_s* p, int clusters, cudaStream_t s) {
 }
 
 int propagate_batch(bpm_plan_s* p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
-                    float* const* d_I, int z_begin, int z_end, cudaStream_t stream) {
+                    float* const* d_I, int z_begin, int z_end, const int* w_begin, const int* w_end,
+                    cudaStream_t stream) {
   const int n = (int)p->inst.size();
   std::vector<InstArgs> args(n);
   std::memset(args.data(), 0, sizeof(InstArgs) * n);
@@ -464,6 +468,8 @@ int propagate_batch(bpm_plan_s* p, const void* const* d_dn, const void* const* d
     a.n = in.d.nx;
     a.z_begin = std::min(z_begin, in.d.nz);
     a.z_end = std::min(z_end, in.d.nz);
+    a.iz0 = w_begin ? w_begin[i] : 0;
+    a.iz1 = w_end ? w_end[i] : in.d.nz;
     const double ph = std::fmod(k0 * in.d.n0 * in.d.dz * (double)(a.z_end - a.z_begin), kTwoPi);
     a.carrier = make_float2((float)std::cos(ph), (float)std::sin(ph));
   }
@@ -562,11 +568,19 @@ extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_in
   return BPM_OK;
 }
 
-extern "C" int bpm_propagate(bpm_plan_t p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
-                             float* const* d_I, int z_begin, int z_end, cudaStream_t stream) {
+namespace {
+
+int propagate_impl(bpm_plan_t p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
+                   float* const* d_I, int z_begin, int z_end, const int* w_begin, const int* w_end,
+                   cudaStream_t stream) {
   if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
   if (!d_dn || !d_Ein || !d_Eout) return fail(BPM_ERR_ARG, "d_dn, d_Ein and d_Eout must be non-NULL arrays");
   if (z_begin < 0 || z_end < z_begin) return fail(BPM_ERR_ARG, "need 0 <= z_begin <= z_end");
+  if ((w_begin == nullptr) != (w_end == nullptr)) return fail(BPM_ERR_ARG, "give both window arrays or neither");
+  if (w_begin)
+    for (size_t i = 0; i < p->inst.size(); ++i)
+      if (w_begin[i] < 0 || w_end[i] < w_begin[i])
+        return fail(BPM_ERR_ARG, "instance %zu: need 0 <= w_begin <= w_end", i);
   for (size_t i = 0; i < p->inst.size(); ++i) {
     const InstPlan& in = p->inst[i];
     const int zb = std::min(z_begin, in.d.nz), ze = std::min(z_end, in.d.nz);
@@ -576,7 +590,7 @@ extern "C" int bpm_propagate(bpm_plan_t p, const void* const* d_dn, const void* 
       return fail(BPM_ERR_ALIGN, "instance %zu: device pointers must be 16-byte aligned", i);
   }
   if (p->inst.size() > 1) {
-    int rc = propagate_batch(p, d_dn, d_Ein, d_Eout, d_I, z_begin, z_end, stream);
+    int rc = propagate_batch(p, d_dn, d_Ein, d_Eout, d_I, z_begin, z_end, w_begin, w_end, stream);
     if (rc) return rc;
     return finish_call(p, stream);
   }
@@ -595,6 +609,8 @@ extern "C" int bpm_propagate(bpm_plan_t p, const void* const* d_dn, const void* 
     a.ein = static_cast<const float2*>(d_Ein[i]);
     a.dn = static_cast<const __half*>(d_dn[i]);
     a.inten = d_I ? d_I[i] : nullptr;
+    a.iz0 = w_begin ? w_begin[i] : 0;
+    a.iz1 = w_end ? w_end[i] : in.d.nz;
     a.z_begin = zb;
     a.z_end = ze;
     const double k0 = kTwoPi / in.d.lambda;
@@ -603,6 +619,54 @@ extern "C" int bpm_propagate(bpm_plan_t p, const void* const* d_dn, const void* 
     int rc = dispatch_propagate(p, r, a, stream);
     if (rc) return rc;
   }
+  return finish_call(p, stream);
+}
+
+}  // namespace
+
+extern "C" int bpm_propagate(bpm_plan_t p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
+                             float* const* d_I, int z_begin, int z_end, cudaStream_t stream) {
+  return propagate_impl(p, d_dn, d_Ein, d_Eout, d_I, z_begin, z_end, nullptr, nullptr, stream);
+}
+
+extern "C" int bpm_propagate_window(bpm_plan_t p, const void* const* d_dn, const void* const* d_Ein,
+                                    void* const* d_Eout, float* const* d_I, int z_begin, int z_end,
+                                    const int* h_w_begin, const int* h_w_end, cudaStream_t stream) {
+  if (!h_w_begin || !h_w_end) return fail(BPM_ERR_ARG, "h_w_begin and h_w_end must be non-NULL");
+  return propagate_impl(p, d_dn, d_Ein, d_Eout, d_I, z_begin, z_end, h_w_begin, h_w_end, stream);
+}
+
+extern "C" int bpm_demultiplex(bpm_plan_t p, int inst, const float* d_I, int w_begin, int w_nz, int n_foci,
+                               const int* h_foci, int px, int py, int pz, float* d_out, cudaStream_t stream) {
+  if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
+  if (inst < 0 || inst >= (int)p->inst.size()) return fail(BPM_ERR_ARG, "instance %d out of range", inst);
+  if (w_begin < 0 || w_nz < 0) return fail(BPM_ERR_ARG, "need w_begin >= 0 and w_nz >= 0");
+  if (n_foci < 0 || n_foci > (1 << 24)) return fail(BPM_ERR_ARG, "n_foci must be in [0, 2^24]");
+  if (px < 1 || py < 1 || pz < 1 || (long long)px * py * pz > (1LL << 30))
+    return fail(BPM_ERR_ARG, "patch sizes must be positive and hold at most 2^30 voxels");
+  if (n_foci == 0) return finish_call(p, stream);
+  if (!h_foci || !d_out || (w_nz > 0 && !d_I)) return fail(BPM_ERR_ARG, "NULL pointer");
+  const int n = p->inst[inst].d.nx;
+  for (int j = 0; j < n_foci; ++j) {
+    const int x = h_foci[3 * j], y = h_foci[3 * j + 1];
+    if (x < 0 || x >= n || y < 0 || y >= n) return fail(BPM_ERR_ARG, "focus %d lies outside the grid", j);
+  }
+  if ((int)(3 * (size_t)n_foci) > p->demux_cap) {
+    BPM_CU(cudaStreamSynchronize(stream));
+    cudaFree(p->demux_foci);
+    p->demux_foci = nullptr;
+    p->demux_cap = 0;
+    BPM_CU(cudaMalloc(&p->demux_foci, 3 * (size_t)n_foci * sizeof(int)));
+    p->demux_cap = 3 * n_foci;
+  }
+  // staged through a pageable copy, so the copy completes before the call
+  // returns and the caller may reuse h_foci (pinned or not)
+  const std::vector<int> foci(h_foci, h_foci + 3 * (size_t)n_foci);
+  BPM_CU(cudaMemcpyAsync(p->demux_foci, foci.data(), foci.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+  const long long total = (long long)px * py * pz * n_foci;
+  const int grid = (int)std::min<long long>((total + kThreads - 1) / kThreads, (long long)p->sms * 16);
+  bpm_demux_kernel<<<grid, kThreads, 0, stream>>>(d_I, n, w_begin, w_nz, p->demux_foci, n_foci, px, py, pz, d_out);
+  BPM_CU(cudaGetLastError());
   return finish_call(p, stream);
 }
 
@@ -1017,6 +1081,8 @@ int static_propagate(const bpm_instance_desc& d, unsigned char* scratch, const v
   a.ein = static_cast<const float2*>(d_Ein);
   a.dn = static_cast<const __half*>(d_dn);
   a.inten = d_I;
+  a.iz0 = 0;
+  a.iz1 = d.nz;
   a.z_begin = zb;
   a.z_end = ze;
   const double ph = std::fmod(k0 * d.n0 * d.dz * (double)(ze - zb), kTwoPi);

@@ -237,7 +237,8 @@ struct StepArgs {
   float2* work;            // [n][n] working field; holds E_out at the end
   const float2* ein;       // [n][n] input field (read once)
   const __half* dn;        // [nz][n][n] index volume (dn = n - n0)
-  float* inten;            // [nz][n][n] or nullptr
+  float* inten;            // [iz1 - iz0][n][n] or nullptr
+  int iz0, iz1;            // intensity window: slice z in [iz0, iz1) goes to inten[z - iz0]
   const float2* ht;        // [n][n] propagator, transposed: ht[kx * n + ky]
   const float2* tw;        // twiddles: forward table then inverse table
   float screen_c;          // k0 dz
@@ -454,8 +455,8 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
       }
       const __half* sdn = st.dn ? st.dn + (size_t)((active ? row : r0) - r0) * N : nullptr;
       float* irow = nullptr;
-      if (active && a.inten)
-        irow = st.inten ? st.inten + (size_t)(row - r0) * N : a.inten + ((size_t)z * N + row) * N;
+      if (active && a.inten && z >= a.iz0 && z < a.iz1)
+        irow = st.inten ? st.inten + (size_t)(row - r0) * N : a.inten + ((size_t)(z - a.iz0) * N + row) * N;
       const bool i_smem = st.inten != nullptr;
       // phase screen exp(i k0 dn dz) and |E|^2 on the natural-order field;
       // the evaluation of the phasor (polynomial or sincosf) is chosen once per
@@ -769,11 +770,12 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
     if (__syncthreads_or(!ok)) break;
     if (!last) row_half_step<N, ROW_STEP>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
     else row_half_step<N, ROW_LAST>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
-    if (st.inten) {
+    if (st.inten && z >= a.iz0 && z < a.iz1) {
       fence_proxy_async_smem();
       __syncthreads();
       if (threadIdx.x == 0 && nrow > 0)
-        bulk_store(a.inten + ((size_t)z * N + lo) * N, st.inten, (unsigned)((size_t)nrow * N * sizeof(float)));
+        bulk_store(a.inten + ((size_t)(z - a.iz0) * N + lo) * N, st.inten,
+                   (unsigned)((size_t)nrow * N * sizeof(float)));
     }
     if (!last && !team_barrier(a, epoch, &s_flag)) break;
   }
@@ -964,6 +966,7 @@ struct InstArgs {
   float screen_c;
   float2 carrier;
   int n, z_begin, z_end;
+  int iz0, iz1;             // intensity window (as in StepArgs)
 };
 
 struct BatchArgs {
@@ -1006,6 +1009,8 @@ __device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int
   a.ein = ia.ein;
   a.dn = ia.dn;
   a.inten = ia.inten;
+  a.iz0 = ia.iz0;
+  a.iz1 = ia.iz1;
   a.ht = ia.ht;
   a.tw = ia.tw;
   a.screen_c = ia.screen_c;
@@ -1059,6 +1064,33 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_batch_kernel(BatchArgs b) {
     }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(b.err, 0, kDevErrNan);
+}
+
+// Per-focus patches of an intensity window (PSF de-multiplexing): thread i
+// of the grid-stride loop writes out[i], i = ((j pz + k) py + y) px + x, from
+// voxel (iz_j - pz/2 + k, iy_j - py/2 + y, ix_j - px/2 + x) of the volume,
+// laterally periodic (the grid's boundary condition); slices outside the
+// window [w0, w0 + wnz) give 0.  foci: (ix, iy, iz) triples.
+__global__ void bpm_demux_kernel(const float* __restrict__ I, int n, int w0, int wnz, const int* __restrict__ foci,
+                                 int n_foci, int px, int py, int pz, float* __restrict__ out) {
+  const long long per = (long long)px * py * pz;
+  const long long total = per * n_foci;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / per);
+    long long r = i - (long long)j * per;
+    const int k = (int)(r / ((long long)px * py));
+    r -= (long long)k * px * py;
+    const int y = (int)(r / px), x = (int)(r - (long long)y * px);
+    const int z = foci[3 * j + 2] - pz / 2 + k - w0;
+    float v = 0.f;
+    if (z >= 0 && z < wnz) {
+      const int yy = ((foci[3 * j + 1] - py / 2 + y) % n + n) % n;
+      const int xx = ((foci[3 * j] - px / 2 + x) % n + n) % n;
+      v = __ldcs(I + ((size_t)z * n + yy) * n + xx);
+    }
+    __stcs(out + i, v);
+  }
 }
 
 }  // namespace bpmk

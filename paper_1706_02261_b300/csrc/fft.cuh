@@ -355,7 +355,9 @@ struct LoopFFT {
 #pragma unroll
     for (int b = 0; b < B; ++b) Dft<R, -1>::run(v + b * R);
     if (p + 1 < NP) {
-      const int lg = p * LGR;                 // Ns = R^p = 1 << lg
+      // Ns = R^p = 1 << lg; with two passes only pass 0 exchanges, so the
+      // store addresses are compile-time offsets from the thread's base
+      const int lg = NP == 2 ? 0 : p * LGR;
 #pragma unroll
       for (int b = 0; b < B; ++b) {
         const int j = t + b * T;
