@@ -52,9 +52,10 @@ def _load():
         lib.oracle_dft2.argtypes = [i, i, p, i]
         lib.oracle_propagator.argtypes = [i, i, d, d, d, d, d, p]
         lib.oracle_bpm.argtypes = [i, i, i, d, d, d, d, d, p, p, p, p]
+        lib.oracle_bpm_adaptive.argtypes = [i, i, i, d, d, d, d, d, p, p, p, p]
         lib.oracle_multiplex_psf.argtypes = [i, i, d, d, d, d, i, p, p, p, p, d, p]
         lib.oracle_light_sheet.argtypes = [i, i, d, d, d, d, d, d, p]
-        for f in (lib.oracle_dft1, lib.oracle_dft2, lib.oracle_propagator, lib.oracle_bpm,
+        for f in (lib.oracle_dft1, lib.oracle_dft2, lib.oracle_propagator, lib.oracle_bpm, lib.oracle_bpm_adaptive,
                   lib.oracle_multiplex_psf, lib.oracle_light_sheet):
             f.restype = i
         lib.oracle_num_threads.restype = i
@@ -102,11 +103,13 @@ def propagator(nx, ny, dx, dy, dz, lam, n0) -> np.ndarray:
     return H
 
 
-def bpm(dn, E0, dx, dy, dz, lam, n0, want_intensity: bool = True):
+def bpm(dn, E0, dx, dy, dz, lam, n0, want_intensity: bool = True, adaptive: bool = False):
     """Split-step BPM through every slice of ``dn`` ([nz][ny][nx], n - n0).
 
     Returns ``(E_out, I)`` where ``I`` is the [nz][ny][nx] volume of |E|^2 after
-    each slice's screen (``None`` when ``want_intensity`` is false).
+    each slice's screen (``None`` when ``want_intensity`` is false).  With
+    ``adaptive`` the locally adapted expansion of reading B (per-slice mean
+    index as the reference, first-order corrected propagator) is used.
     """
     dn = np.ascontiguousarray(dn, dtype=np.float64)
     nz, ny, nx = dn.shape
@@ -114,8 +117,8 @@ def bpm(dn, E0, dx, dy, dz, lam, n0, want_intensity: bool = True):
     assert E0.shape == (ny, nx)
     Eout = np.zeros((ny, nx), np.complex128)
     I = np.zeros((nz, ny, nx), np.float64) if want_intensity else None
-    rc = _load().oracle_bpm(nx, ny, nz, dx, dy, dz, lam, n0, _ptr(dn), _ptr(E0), _ptr(Eout),
-                            _ptr(I) if I is not None else None)
+    fn = _load().oracle_bpm_adaptive if adaptive else _load().oracle_bpm
+    rc = fn(nx, ny, nz, dx, dy, dz, lam, n0, _ptr(dn), _ptr(E0), _ptr(Eout), _ptr(I) if I is not None else None)
     _check(rc, "bpm")
     return Eout, I
 

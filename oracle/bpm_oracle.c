@@ -19,6 +19,19 @@
  *       E <- E * exp(i k0 dn[z] dz)        (phase screen, dn = n - n0)
  *       I[z] = |E|^2
  *
+ * Locally adapted expansion, reading B (oracle_bpm_adaptive).  The method
+ * paragraph pairs the exact propagator with "a locally adapted expansion of
+ * refractive indices" (its supplementary notes are not available).  Reading B
+ * takes, per slice, the slice's mean index n0 + delta_z as the reference:
+ *   delta_z = (1 / (nx ny)) sum over the slice of dn[z]
+ *   H_z(kx,ky) = exp(i (kz0 + delta_z k0^2 n0 / kz0) dz)  if kz0^2 > 0, else 0,
+ *            kz0 = sqrt(K^2 - kx^2 - ky^2)
+ *     (the exact propagator of the medium n0 + delta_z to first order in
+ *      delta_z: d kz / d n = k0^2 n / kz)
+ *   E <- IDFT2( H_z * DFT2(E) ),  E <- E * exp(i k0 (dn[z] - delta_z) dz)
+ * so a slice of uniform index is propagated by the propagator of its own
+ * medium (to first order) instead of the background's propagator and a screen.
+ *
  * Every step follows that definition literally: no carrier factoring, no fused
  * passes, no reordering.  The DFT is a recursive mixed-radix decimation in time
  * (smallest prime factor first, a direct O(n^2) sum for prime lengths), with
@@ -168,6 +181,54 @@ int oracle_propagator(int nx, int ny, double dx, double dy, double dz,
             H[(size_t)y * nx + x] = (kz2 > 0) ? cexp(I * sqrt(kz2) * dz) : 0;
         }
     }
+    return 0;
+}
+
+/* Reading B of the locally adapted expansion (see the header): per slice the
+ * mean index step delta_z, the propagator corrected to first order in
+ * delta_z, and the screen of dn - delta_z.  Arguments as oracle_bpm. */
+int oracle_bpm_adaptive(int nx, int ny, int nz, double dx, double dy, double dz,
+                        double lambda, double n0, const double *dn, const double *E0v,
+                        double *Eoutv, double *Iout)
+{
+    if (nx < 1 || ny < 1 || nz < 0 || !(dz > 0) || !(dx > 0) || !(dy > 0) || !(lambda > 0) || !(n0 > 0))
+        return -1;
+    size_t M = (size_t)nx * ny;
+    cplx *E = (cplx *)malloc(sizeof(cplx) * M);
+    double *kz0 = (double *)malloc(sizeof(double) * M);   /* 0 marks a cut component */
+    double k0 = kTwoPi / lambda, K = k0 * n0;
+    for (int y = 0; y < ny; ++y) {
+        double ky = grid_k(y, ny, dy);
+        for (int x = 0; x < nx; ++x) {
+            double kx = grid_k(x, nx, dx);
+            double kz2 = K * K - kx * kx - ky * ky;
+            kz0[(size_t)y * nx + x] = (kz2 > 0) ? sqrt(kz2) : 0.0;
+        }
+    }
+    memcpy(E, E0v, sizeof(cplx) * M);
+    for (int z = 0; z < nz; ++z) {
+        const double *slice = dn + (size_t)z * M;
+        double sum = 0.0;
+        for (size_t i = 0; i < M; ++i) sum += slice[i];
+        const double delta = sum / (double)M;
+        oracle_dft2(nx, ny, (double *)E, -1);
+#pragma omp parallel for schedule(static)
+        for (long long i = 0; i < (long long)M; ++i) {
+            const double kz = kz0[i];
+            E[i] = (kz > 0) ? E[i] * cexp(I * (kz + delta * k0 * k0 * n0 / kz) * dz) : 0;
+        }
+        oracle_dft2(nx, ny, (double *)E, +1);
+#pragma omp parallel for schedule(static)
+        for (long long i = 0; i < (long long)M; ++i) {
+            cplx e = E[i] / (double)M;
+            e *= cexp(I * k0 * (slice[i] - delta) * dz);
+            E[i] = e;
+            if (Iout) Iout[(size_t)z * M + (size_t)i] = creal(e) * creal(e) + cimag(e) * cimag(e);
+        }
+    }
+    memcpy(Eoutv, E, sizeof(cplx) * M);
+    free(kz0);
+    free(E);
     return 0;
 }
 

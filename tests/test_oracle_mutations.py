@@ -10,6 +10,7 @@ import types
 import pytest
 
 import oracle
+import tests.test_oracle_adaptive as t_ada
 import tests.test_oracle_fft as t_fft
 import tests.test_oracle_propagation as t_prop
 import tests.test_oracle_synthesis as t_syn
@@ -34,6 +35,9 @@ MUTATIONS = [
     ("pupil radius from K", "if (kp2 <= kna * kna && K * K - kp2 > 0) ++n_pupil;", "if (kp2 <= K * K && K * K - kp2 > 0) ++n_pupil;"),
     ("light-sheet waist", "w0 = lambda / (M_PI * NA);", "w0 = lambda / (2 * M_PI * NA);"),
     ("light-sheet centre", "double xc = (double)(nx / 2) * dx;", "double xc = (double)(nx / 2 + 1) * dx;"),
+    ("adapted propagator correction sign", "cexp(I * (kz + delta * k0 * k0 * n0 / kz) * dz)",
+     "cexp(I * (kz - delta * k0 * k0 * n0 / kz) * dz)"),
+    ("adapted screen keeps the mean", "e *= cexp(I * k0 * (slice[i] - delta) * dz);", "e *= cexp(I * k0 * slice[i] * dz);"),
 ]
 
 PINS = [
@@ -42,7 +46,8 @@ PINS = [
     t_prop.test_gaussian_beam_matches_angular_spectrum_quadrature,
     t_prop.test_screen_acts_after_diffraction_within_a_slice, t_syn.test_multiplex_equals_direct_sum,
     t_syn.test_each_focus_has_unit_energy, t_syn.test_single_focus_forms_at_its_depth_and_position,
-    t_syn.test_light_sheet_focus_profile,
+    t_syn.test_light_sheet_focus_profile, t_ada.test_zero_mean_slices_give_reading_a,
+    t_ada.test_uniform_slices_tilted_plane_wave_closed_forms, t_ada.test_reading_b_beats_reading_a_in_a_uniform_medium,
 ]
 
 
@@ -71,7 +76,7 @@ def test_pins_catch_mutation(tmp_path, monkeypatch, tag, find, repl):
     mod = _mutated_oracle(tmp_path, find, repl, tag)
     failed = []
     for pin in PINS:
-        for m in (t_fft, t_prop, t_syn):
+        for m in (t_fft, t_prop, t_syn, t_ada):
             monkeypatch.setattr(m, "oracle", mod)
         try:
             if pin is t_fft.test_dft_matches_numpy:
