@@ -55,6 +55,14 @@ enum {
                                         persistent kernel (comparison path)           */
 #define BPM_FLAG_GRAPH         0x4u  /* batched plans: capture the launch in a CUDA graph
                                         once per argument set and replay it          */
+#define BPM_FLAG_ADAPTIVE      0x8u  /* single-instance plans: locally adapted expansion
+                                        of the index (method paragraph), reading B:
+                                        slice z takes its mean index step delta_z as
+                                        reference, propagator H exp(i delta_z k0^2 n0
+                                        dz / kz0) (exact medium n0 + delta_z to first
+                                        order), screen exp(i k0 (dn - delta_z) dz); the
+                                        means are computed on the device per call
+                                        (one extra read of the index slices)          */
 
 typedef struct bpm_plan_s *bpm_plan_t;
 

@@ -30,6 +30,7 @@ BPM_ERR_UNSUPPORTED = -6
 BPM_FLAG_SYNC = 0x1
 BPM_FLAG_MULTI_LAUNCH = 0x2
 BPM_FLAG_GRAPH = 0x4
+BPM_FLAG_ADAPTIVE = 0x8
 
 SUPPORTED_N = (64, 128, 192, 256, 384, 512, 1024)
 

@@ -127,6 +127,8 @@ struct NRes {
 struct InstPlan {
   bpm_instance_desc d;
   float2* ht = nullptr;
+  float* gt = nullptr;      // BPM_FLAG_ADAPTIVE: k0^2 n0 dz / kz0, laid out like ht
+  float* delta = nullptr;   // BPM_FLAG_ADAPTIVE: mean index step per slice [nz]
 };
 
 struct bpm_plan_s {
@@ -244,7 +246,11 @@ int check_desc(const bpm_instance_desc& d, int i) {
 
 void free_plan(bpm_plan_s* p) {
   if (!p) return;
-  for (auto& in : p->inst) cudaFree(in.ht);
+  for (auto& in : p->inst) {
+    cudaFree(in.ht);
+    cudaFree(in.gt);
+    cudaFree(in.delta);
+  }
   for (auto& kv : p->res) {
     cudaFree(kv.second.tw);
     cudaFree(kv.second.tmp);
@@ -305,7 +311,7 @@ int launch_propagate(bpm_plan_s* p, const NRes& r, StepArgs a, cudaStream_t s) {
   if (p->flags & BPM_FLAG_MULTI_LAUNCH) {
     bpm_row_kernel<N, ROW_FWD><<<G, kThreads, r.smem, s>>>(a, a.z_begin);
     for (int z = a.z_begin; z < a.z_end; ++z) {
-      bpm_col_kernel<N, COL_PROP><<<G, kThreads, r.smem, s>>>(a);
+      bpm_col_kernel<N, COL_PROP><<<G, kThreads, r.smem, s>>>(a, z);
       if (z + 1 < a.z_end) bpm_row_kernel<N, ROW_STEP><<<G, kThreads, r.smem, s>>>(a, z);
       else bpm_row_kernel<N, ROW_LAST><<<G, kThreads, r.smem, s>>>(a, z);
     }
@@ -323,7 +329,7 @@ template <int N>
 int launch_synth_group(bpm_plan_s*, const NRes& r, StepArgs a, cudaStream_t s) {
   const int G = r.team;
   bpm_row_kernel<N, ROW_FWD><<<G, kThreads, r.smem, s>>>(a, 0);
-  bpm_col_kernel<N, COL_FOCUS><<<G, kThreads, r.smem, s>>>(a);
+  bpm_col_kernel<N, COL_FOCUS><<<G, kThreads, r.smem, s>>>(a, 0);
   bpm_row_kernel<N, ROW_INV_ACC><<<G, kThreads, r.smem, s>>>(a, 0);
   BPM_CU(cudaGetLastError());
   return BPM_OK;
@@ -519,8 +525,10 @@ extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_in
   if (!out) return fail(BPM_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!inst || n_inst < 1 || n_inst > 4096) return fail(BPM_ERR_ARG, "n_inst must be in [1, 4096]");
-  if (flags & ~(BPM_FLAG_SYNC | BPM_FLAG_MULTI_LAUNCH | BPM_FLAG_GRAPH))
+  if (flags & ~(BPM_FLAG_SYNC | BPM_FLAG_MULTI_LAUNCH | BPM_FLAG_GRAPH | BPM_FLAG_ADAPTIVE))
     return fail(BPM_ERR_ARG, "unknown flag bits 0x%x", flags);
+  if ((flags & BPM_FLAG_ADAPTIVE) && n_inst > 1)
+    return fail(BPM_ERR_UNSUPPORTED, "BPM_FLAG_ADAPTIVE takes single-instance plans");
   for (int i = 0; i < n_inst; ++i) {
     int rc = check_desc(inst[i], i);
     if (rc) return rc;
@@ -551,11 +559,27 @@ extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_in
     }
     const size_t M = (size_t)n * n;
     if (!cu(cudaMalloc(&ip.ht, M * sizeof(float2)), "cudaMalloc(propagator)")) break;
+    if (flags & BPM_FLAG_ADAPTIVE) {
+      if (!cu(cudaMalloc(&ip.gt, M * sizeof(float)), "cudaMalloc(adapted propagator rates)")) {
+        cudaFree(ip.ht);
+        break;
+      }
+      if (!cu(cudaMalloc(&ip.delta, std::max(1, inst[i].nz) * sizeof(float)), "cudaMalloc(slice means)")) {
+        cudaFree(ip.ht);
+        cudaFree(ip.gt);
+        break;
+      }
+    }
     p->inst.push_back(ip);
     const int threads = 256;
     bpm_build_ht_kernel<<<(unsigned)((M + threads - 1) / threads), threads, 0, stream>>>(
         ip.ht, inst[i].nx, inst[i].ny, inst[i].dx, inst[i].dy, inst[i].dz, inst[i].lambda, inst[i].n0);
     cu(cudaGetLastError(), "bpm_build_ht_kernel");
+    if (ip.gt) {
+      bpm_build_gt_kernel<<<(unsigned)((M + threads - 1) / threads), threads, 0, stream>>>(
+          ip.gt, inst[i].nx, inst[i].ny, inst[i].dx, inst[i].dy, inst[i].dz, inst[i].lambda, inst[i].n0);
+      cu(cudaGetLastError(), "bpm_build_gt_kernel");
+    }
   }
   if (rc == BPM_OK && n_inst > 1) rc = setup_batch(p);
   if (rc == BPM_OK) cu(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
@@ -613,6 +637,15 @@ int propagate_impl(bpm_plan_t p, const void* const* d_dn, const void* const* d_E
     a.iz1 = w_end ? w_end[i] : in.d.nz;
     a.z_begin = zb;
     a.z_end = ze;
+    if (in.delta) {
+      // reading B: mean index step of slices [zb, ze) before the propagation
+      // (delta is indexed by absolute slice, as dn is)
+      bpm_slice_mean_kernel<<<ze - zb, kThreads, 0, stream>>>(a.dn + (size_t)zb * in.d.nx * in.d.ny,
+                                                              (size_t)in.d.nx * in.d.ny, in.delta + zb);
+      BPM_CU(cudaGetLastError());
+      a.delta = in.delta;
+      a.gt = in.gt;
+    }
     const double k0 = kTwoPi / in.d.lambda;
     double ph = std::fmod(k0 * in.d.n0 * in.d.dz * (double)(ze - zb), kTwoPi);
     a.carrier = make_float2((float)std::cos(ph), (float)std::sin(ph));

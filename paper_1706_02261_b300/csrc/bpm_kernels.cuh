@@ -239,6 +239,12 @@ struct StepArgs {
   const __half* dn;        // [nz][n][n] index volume (dn = n - n0)
   float* inten;            // [iz1 - iz0][n][n] or nullptr
   int iz0, iz1;            // intensity window: slice z in [iz0, iz1) goes to inten[z - iz0]
+  // locally adapted expansion (reading B), nullptr when off: the mean index
+  // step of each slice and G = k0^2 n0 dz / kz0 per component, transposed
+  // like ht; slice z's propagator is H exp(i delta[z] G), its screen acts on
+  // dn - delta[z]
+  const float* delta;
+  const float* gt;
   const float2* ht;        // [n][n] propagator, transposed: ht[kx * n + ky]
   const float2* tw;        // twiddles: forward table then inverse table
   float screen_c;          // k0 dz
@@ -374,6 +380,32 @@ __device__ __forceinline__ bool team_barrier(const StepArgs& a, unsigned& epoch,
   return *s_flag != 0;
 }
 
+// First-order correction of the propagator to slice z's mean index (reading
+// B): w[k] *= exp(i dl g(k)), k < count, with g(k) read by gk(k).  The phasor
+// evaluation is chosen once per warp from the largest |phase| (all lanes of
+// the warp call this together).
+template <int COUNT, class GK>
+__device__ __forceinline__ void adapt_multiply(float2* w, float dl, GK&& gk) {
+  float ph[COUNT];
+  float mx = 0.f;
+#pragma unroll
+  for (int k = 0; k < COUNT; ++k) {
+    ph[k] = dl * gk(k);
+    mx = fmaxf(mx, fabsf(ph[k]));
+  }
+  const int range = phasor_range(mx);
+  if (range == 0) {
+#pragma unroll
+    for (int k = 0; k < COUNT; ++k) w[k] = cmul(w[k], unit_phasor_small(ph[k]));
+  } else if (range == 1) {
+#pragma unroll
+    for (int k = 0; k < COUNT; ++k) w[k] = cmul(w[k], unit_phasor_poly(ph[k]));
+  } else {
+#pragma unroll
+    for (int k = 0; k < COUNT; ++k) w[k] = cmul(w[k], unit_phasor_libm(ph[k]));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // half-steps
 // ---------------------------------------------------------------------------
@@ -473,12 +505,16 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
           sum += dval[q];
         }
         bad |= active && !isfinite(sum);
-        const int range = phasor_range(a.screen_c * mx);
+        // reading B: the screen acts on dn - delta[z] (the slice's mean index
+        // step went into the propagator)
+        const float off = a.delta ? a.delta[z] : 0.f;
+        const float c0 = -a.screen_c * off;
+        const int range = phasor_range(a.screen_c * (mx + fabsf(off)));
         auto body = [&](auto phasor) {
 #pragma unroll
           for (int q = 0; q < C::PTS; ++q) {
             const int x = layout_index<N, C::T, C::R0>(q, t);
-            const float2 e = cmul(w[q], phasor(a.screen_c * dval[q]));
+            const float2 e = cmul(w[q], phasor(fmaf(a.screen_c, dval[q], c0)));
             w[q] = e;
             if (irow) {
               const float iv = fmaf(e.x, e.x, e.y * e.y);
@@ -531,7 +567,7 @@ __device__ __forceinline__ void four_step_fwd(float2* v, const float2* tw, float
 // propagator H^T[col][ky], inverse FFT_y (conjugated forward), store, NG
 // columns per round, all in registers apart from the two exchanges.
 template <int N>
-__device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int c1, float2* s_buf,
+__device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int c1, int z, float2* s_buf,
                                                  const float2* s_tw4, const Stage& st) {
   using C = Cfg<N>;
   constexpr int N1 = C::FS_N1, NG = C::NG, SA = C::FS_SA, SC = C::FS_SC;
@@ -561,6 +597,10 @@ __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int 
 #pragma unroll
       for (int k = 0; k < N1; ++k) v[k] = cmul(v[k], __ldg(h + N1 * k));
     }
+    if (a.delta) {
+      const float* g = a.gt + (size_t)(on ? col : c0) * N + ai;
+      adapt_multiply<N1>(v, a.delta[z], [&](int k) { return __ldg(g + N1 * k); });
+    }
     conj_all(v, N1);
     four_step_fwd<N1, SA>(v, tw, xw, xr);
     conj_all(v, N1);
@@ -580,12 +620,12 @@ __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int 
 // forward transform's exchange buffer).  Sizes with a four-step layout take
 // col_half_step_4s for the propagator.
 template <int N, int MODE>
-__device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1, float2* s_buf,
+__device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1, int z, float2* s_buf,
                                               const float2* s_twf, const float2* s_twi,
                                               const Stage& st = Stage()) {
   using C = Cfg<N>;
   if constexpr (C::FS_N1 > 0 && MODE == COL_PROP) {
-    col_half_step_4s<N>(a, c0, c1, s_buf, s_twi + C::TWI, st);
+    col_half_step_4s<N>(a, c0, c1, z, s_buf, s_twi + C::TWI, st);
     return;
   }
   const int lane = threadIdx.x & 31;
@@ -634,6 +674,10 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
         } else {
 #pragma unroll
           for (int q = 0; q < C::PTS; ++q) w[q] = cmul(w[q], __ldg(hcol + layout_index<N, C::T, C::RL>(q, t)));
+        }
+        if (a.delta) {
+          const float* g = a.gt + (size_t)(active ? col : c0) * N;
+          adapt_multiply<C::PTS>(w, a.delta[z], [&](int q) { return __ldg(g + layout_index<N, C::T, C::RL>(q, t)); });
         }
       });
     } else {
@@ -698,6 +742,55 @@ __device__ __forceinline__ void report_bad(const StepArgs& a, bool bad) {
 // kernels
 // ---------------------------------------------------------------------------
 
+// Mean index step of every slice (reading B): CTA z sums slice z0 + z of the
+// FP16 volume (FP32 partial sums of at most M / kThreads values per thread,
+// FP64 across the block) into delta[z].
+__global__ void __launch_bounds__(kThreads) bpm_slice_mean_kernel(const __half* __restrict__ dn, size_t M,
+                                                                  float* __restrict__ delta) {
+  const __half* slice = dn + (size_t)blockIdx.x * M;
+  float acc = 0.f;
+  const size_t M8 = M / 8;   // 16-byte loads of 8 values (M is a multiple of 8)
+  for (size_t i = threadIdx.x; i < M8; i += kThreads) {
+    const uint4 u = __ldcs(reinterpret_cast<const uint4*>(slice) + i);
+    const __half2* h = reinterpret_cast<const __half2*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __half22float2(h[k]);
+      acc += f.x + f.y;
+    }
+  }
+  for (size_t i = M8 * 8 + threadIdx.x; i < M; i += kThreads) acc += __half2float(slice[i]);
+  __shared__ double part[kWarps];
+  double d = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += part[w];
+    delta[blockIdx.x] = (float)(t / (double)M);
+  }
+}
+
+// G = k0^2 n0 dz / kz0 per component (0 where the propagator is cut), laid out
+// like ht ([kx][ky]); the cut is decided exactly as in bpm_build_ht_kernel.
+__global__ void bpm_build_gt_kernel(float* gt, int nx, int ny, double dx, double dy, double dz, double lambda,
+                                    double n0) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)nx * ny) return;
+  const int kyi = (int)(i % ny), kxi = (int)(i / ny);
+  const int fx = kxi < (nx + 1) / 2 ? kxi : kxi - nx;
+  const int fy = kyi < (ny + 1) / 2 ? kyi : kyi - ny;
+  const double twopi = 6.283185307179586;
+  const double k0 = __ddiv_rn(twopi, lambda);
+  const double K = __dmul_rn(k0, n0);
+  const double kx = __ddiv_rn(__dmul_rn(twopi, (double)fx), __dmul_rn((double)nx, dx));
+  const double ky = __ddiv_rn(__dmul_rn(twopi, (double)fy), __dmul_rn((double)ny, dy));
+  const double kz2 = __dsub_rn(__dsub_rn(__dmul_rn(K, K), __dmul_rn(kx, kx)), __dmul_rn(ky, ky));
+  gt[i] = kz2 > 0.0 ? (float)(k0 * k0 * n0 * dz / sqrt(kz2)) : 0.f;
+}
+
 // The whole slice loop in one cooperative launch; gridDim.x CTAs form the team
 // (rows split evenly, columns in aligned groups of NG).
 // Shared memory: twiddles | group buffers | [propagator columns of this CTA]
@@ -758,7 +851,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
       }
       dn_pending = true;
     }
-    col_half_step<N, COL_PROP>(a, clo, chi, s_buf, s_twf, s_twi, st);
+    col_half_step<N, COL_PROP>(a, clo, chi, z, s_buf, s_twf, s_twi, st);
     if (!team_barrier(a, epoch, &s_flag)) break;
     bool ok = true;
     if (dn_pending) {
@@ -803,7 +896,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_row_kernel(StepArgs a, int z)
 }
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(kThreads, 1) bpm_col_kernel(StepArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) bpm_col_kernel(StepArgs a, int z) {
   using C = Cfg<N>;
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
@@ -812,7 +905,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_col_kernel(StepArgs a) {
   load_twiddles<N>(a, s_twf, s_twi);
   const int G = gridDim.x, rank = blockIdx.x;
   const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
-  col_half_step<N, MODE>(a, lo, hi, s_buf, s_twf, s_twi);
+  col_half_step<N, MODE>(a, lo, hi, z, s_buf, s_twf, s_twi);
 }
 
 // Light sheet: the ky = 0 spectrum line, inverse FFT_x by group 0 of warp 0,
@@ -1004,7 +1097,7 @@ __device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int
   float2* s_twf = smem;
   float2* s_twi = s_twf + C::TWF;
   float2* s_buf = s_twi + C::TWI + C::TW4;
-  StepArgs a;
+  StepArgs a = {};          // every field not set below is zero / nullptr (e.g. no adapted expansion)
   a.work = ia.work;
   a.ein = ia.ein;
   a.dn = ia.dn;
@@ -1032,7 +1125,7 @@ __device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int
   row_half_step<N, ROW_FWD>(a, lo, hi, a.z_begin, s_buf, s_twf, s_twi, bad);
   cluster_sync_all();
   for (int z = a.z_begin; z < a.z_end; ++z) {
-    col_half_step<N, COL_PROP>(a, lo, hi, s_buf, s_twf, s_twi);
+    col_half_step<N, COL_PROP>(a, lo, hi, z, s_buf, s_twf, s_twi);
     cluster_sync_all();
     if (z + 1 < a.z_end) row_half_step<N, ROW_STEP>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
     else row_half_step<N, ROW_LAST>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
