@@ -133,6 +133,26 @@ int bpm_propagate_window(bpm_plan_t p, const void *const *d_dn, const void *cons
                          void *const *d_Eout, float *const *d_I, int z_begin, int z_end,
                          const int *h_w_begin, const int *h_w_end, cudaStream_t stream);
 
+/* bpm_propagate_reverse - the split-step loop towards -z through slices
+ * z_end-1, z_end-2, ..., z_begin of a single-instance plan (the same
+ * per-slice step: propagator over dz, then the slice's screen), e.g. light
+ * emitted inside the sample travelling back to its surface: the field enters
+ * at the exit plane of slice z_end-1 and d_Eout receives it at the entrance
+ * plane of slice z_begin (with the carrier exp(i k0 n0 dz (z_end - z_begin))).
+ * d_I (nullable) is the [nz][ny][nx] volume; slice z receives |E|^2 after its
+ * screen.  With BPM_FLAG_ADAPTIVE each slice uses its own mean index step.
+ * The paper's adaptive-optics simulation (conjugating the wavefront of a
+ * guide star at the sample surface, Fig. 2c paragraph) is this call,
+ * bpm_phase_conjugate, and a forward bpm_propagate.
+ * Errors: as bpm_propagate; BPM_ERR_UNSUPPORTED for batched plans. */
+int bpm_propagate_reverse(bpm_plan_t p, const void *d_dn, const void *d_Ein, void *d_Eout, float *d_I,
+                          int z_begin, int z_end, cudaStream_t stream);
+
+/* bpm_phase_conjugate - E <- conj(E) in place on instance inst's field (the
+ * time-reversed monochromatic wave).  d_E: device complex float [ny][nx],
+ * 16-byte aligned.  Errors: BPM_ERR_ARG, BPM_ERR_ALIGN, BPM_ERR_CUDA. */
+int bpm_phase_conjugate(bpm_plan_t p, int inst, void *d_E, cudaStream_t stream);
+
 /* bpm_demultiplex - cut one patch per focus out of an intensity window, the
  * de-multiplexing step of the paper's multiplexed PSF calculation (a set of
  * non-overlapping PSFs computed in one propagation is split into the

@@ -310,9 +310,10 @@ int launch_propagate(bpm_plan_s* p, const NRes& r, StepArgs a, cudaStream_t s) {
   const int G = r.team;
   if (p->flags & BPM_FLAG_MULTI_LAUNCH) {
     bpm_row_kernel<N, ROW_FWD><<<G, kThreads, r.smem, s>>>(a, a.z_begin);
-    for (int z = a.z_begin; z < a.z_end; ++z) {
+    for (int zi = a.z_begin; zi < a.z_end; ++zi) {
+      const int z = a.reverse ? a.z_begin + a.z_end - 1 - zi : zi;     // slice crossed by this step
       bpm_col_kernel<N, COL_PROP><<<G, kThreads, r.smem, s>>>(a, z);
-      if (z + 1 < a.z_end) bpm_row_kernel<N, ROW_STEP><<<G, kThreads, r.smem, s>>>(a, z);
+      if (zi + 1 < a.z_end) bpm_row_kernel<N, ROW_STEP><<<G, kThreads, r.smem, s>>>(a, z);
       else bpm_row_kernel<N, ROW_LAST><<<G, kThreads, r.smem, s>>>(a, z);
     }
     BPM_CU(cudaGetLastError());
@@ -596,7 +597,7 @@ namespace {
 
 int propagate_impl(bpm_plan_t p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
                    float* const* d_I, int z_begin, int z_end, const int* w_begin, const int* w_end,
-                   cudaStream_t stream) {
+                   cudaStream_t stream, bool reverse = false) {
   if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
   if (!d_dn || !d_Ein || !d_Eout) return fail(BPM_ERR_ARG, "d_dn, d_Ein and d_Eout must be non-NULL arrays");
   if (z_begin < 0 || z_end < z_begin) return fail(BPM_ERR_ARG, "need 0 <= z_begin <= z_end");
@@ -613,6 +614,7 @@ int propagate_impl(bpm_plan_t p, const void* const* d_dn, const void* const* d_E
     if (!aligned16(d_Ein[i]) || !aligned16(d_Eout[i]) || !aligned16(d_dn[i]) || (d_I && !aligned16(d_I[i])))
       return fail(BPM_ERR_ALIGN, "instance %zu: device pointers must be 16-byte aligned", i);
   }
+  if (reverse && p->inst.size() > 1) return fail(BPM_ERR_UNSUPPORTED, "reverse propagation takes single-instance plans");
   if (p->inst.size() > 1) {
     int rc = propagate_batch(p, d_dn, d_Ein, d_Eout, d_I, z_begin, z_end, w_begin, w_end, stream);
     if (rc) return rc;
@@ -637,6 +639,7 @@ int propagate_impl(bpm_plan_t p, const void* const* d_dn, const void* const* d_E
     a.iz1 = w_end ? w_end[i] : in.d.nz;
     a.z_begin = zb;
     a.z_end = ze;
+    a.reverse = reverse ? 1 : 0;
     if (in.delta) {
       // reading B: mean index step of slices [zb, ze) before the propagation
       // (delta is indexed by absolute slice, as dn is)
@@ -667,6 +670,27 @@ extern "C" int bpm_propagate_window(bpm_plan_t p, const void* const* d_dn, const
                                     const int* h_w_begin, const int* h_w_end, cudaStream_t stream) {
   if (!h_w_begin || !h_w_end) return fail(BPM_ERR_ARG, "h_w_begin and h_w_end must be non-NULL");
   return propagate_impl(p, d_dn, d_Ein, d_Eout, d_I, z_begin, z_end, h_w_begin, h_w_end, stream);
+}
+
+extern "C" int bpm_propagate_reverse(bpm_plan_t p, const void* d_dn, const void* d_Ein, void* d_Eout, float* d_I,
+                                     int z_begin, int z_end, cudaStream_t stream) {
+  const void* dn[1] = {d_dn};
+  const void* ein[1] = {d_Ein};
+  void* eout[1] = {d_Eout};
+  float* inten[1] = {d_I};
+  return propagate_impl(p, dn, ein, eout, d_I ? inten : nullptr, z_begin, z_end, nullptr, nullptr, stream, true);
+}
+
+extern "C" int bpm_phase_conjugate(bpm_plan_t p, int inst, void* d_E, cudaStream_t stream) {
+  if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
+  if (inst < 0 || inst >= (int)p->inst.size()) return fail(BPM_ERR_ARG, "instance %d out of range", inst);
+  if (!d_E) return fail(BPM_ERR_ARG, "d_E is NULL");
+  if (!aligned16(d_E)) return fail(BPM_ERR_ALIGN, "d_E must be 16-byte aligned");
+  const size_t M = (size_t)p->inst[inst].d.nx * p->inst[inst].d.ny;
+  const int grid = (int)std::min<size_t>((M + kThreads - 1) / kThreads, (size_t)p->sms * 8);
+  bpm_conj_kernel<<<grid, kThreads, 0, stream>>>(static_cast<float2*>(d_E), M);
+  BPM_CU(cudaGetLastError());
+  return finish_call(p, stream);
 }
 
 extern "C" int bpm_demultiplex(bpm_plan_t p, int inst, const float* d_I, int w_begin, int w_nz, int n_foci,

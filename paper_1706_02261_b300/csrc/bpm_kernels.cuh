@@ -224,6 +224,22 @@ __device__ __forceinline__ float2 unit_phasor_libm(float x) {
   return make_float2(c, s);
 }
 
+// exp(i x) for any moderate |x| without a branch: Cody-Waite reduction
+// x = q pi/2 + r with q = rint(2x/pi) and pi/2 split into a float head and
+// tail, the Taylor polynomial of unit_phasor_poly on |r| <= pi/4, and the
+// rotation by i^q.  Accurate to FP32 rounding for |x| up to about 1e5.
+__device__ __forceinline__ float2 unit_phasor_reduced(float x) {
+  constexpr float kTwoOverPi = 0.636619772f;
+  constexpr float kHalfPiHi = 1.57079637f;          // float nearest pi/2
+  constexpr float kHalfPiLo = -4.37113883e-8f;      // pi/2 - kHalfPiHi
+  const float q = rintf(x * kTwoOverPi);
+  const float r = fmaf(-q, kHalfPiLo, fmaf(-q, kHalfPiHi, x));
+  const float2 e = unit_phasor_poly(r);
+  const int k = (int)q & 3;
+  const float c = (k & 1) ? e.y : e.x, sn = (k & 1) ? e.x : e.y;
+  return make_float2((k == 1 || k == 2) ? -c : c, (k & 2) ? -sn : sn);
+}
+
 // The evaluation every lane of the warp can use, from each lane's largest
 // |screen phase|: 0 the short polynomial, 1 the long one, 2 sincosf (NaN
 // index values keep a polynomial; they are reported separately).
@@ -245,6 +261,10 @@ struct StepArgs {
   // dn - delta[z]
   const float* delta;
   const float* gt;
+  // propagation towards -z: loop step z handles slice z_begin + z_end - 1 - z
+  // (index, slice mean and intensity of that slice); the field enters at the
+  // exit plane of slice z_end - 1
+  int reverse;
   const float2* ht;        // [n][n] propagator, transposed: ht[kx * n + ky]
   const float2* tw;        // twiddles: forward table then inverse table
   float screen_c;          // k0 dz
@@ -381,29 +401,14 @@ __device__ __forceinline__ bool team_barrier(const StepArgs& a, unsigned& epoch,
 }
 
 // First-order correction of the propagator to slice z's mean index (reading
-// B): w[k] *= exp(i dl g(k)), k < count, with g(k) read by gk(k).  The phasor
-// evaluation is chosen once per warp from the largest |phase| (all lanes of
-// the warp call this together).
+// B): w[k] *= exp(i dl g(k)), k < count, with g(k) read by gk(k).  The phase
+// grows without bound towards the evanescent cut (g ~ 1 / kz0) and every
+// column holds a few such components, so a per-warp choice would always fall
+// to sincosf; the branch-free reduced evaluation serves all elements.
 template <int COUNT, class GK>
 __device__ __forceinline__ void adapt_multiply(float2* w, float dl, GK&& gk) {
-  float ph[COUNT];
-  float mx = 0.f;
 #pragma unroll
-  for (int k = 0; k < COUNT; ++k) {
-    ph[k] = dl * gk(k);
-    mx = fmaxf(mx, fabsf(ph[k]));
-  }
-  const int range = phasor_range(mx);
-  if (range == 0) {
-#pragma unroll
-    for (int k = 0; k < COUNT; ++k) w[k] = cmul(w[k], unit_phasor_small(ph[k]));
-  } else if (range == 1) {
-#pragma unroll
-    for (int k = 0; k < COUNT; ++k) w[k] = cmul(w[k], unit_phasor_poly(ph[k]));
-  } else {
-#pragma unroll
-    for (int k = 0; k < COUNT; ++k) w[k] = cmul(w[k], unit_phasor_libm(ph[k]));
-  }
+  for (int k = 0; k < COUNT; ++k) w[k] = cmul(w[k], unit_phasor_reduced(dl * gk(k)));
 }
 
 // ---------------------------------------------------------------------------
@@ -841,8 +846,9 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
   bool bad = false, dn_pending = false;
   row_half_step<N, ROW_FWD>(a, lo, hi, a.z_begin, s_buf, s_twf, s_twi, bad);
   if (!team_barrier(a, epoch, &s_flag)) return;
-  for (int z = a.z_begin; z < a.z_end; ++z) {
-    const bool last = z + 1 == a.z_end;
+  for (int zi = a.z_begin; zi < a.z_end; ++zi) {
+    const bool last = zi + 1 == a.z_end;
+    const int z = a.reverse ? a.z_begin + a.z_end - 1 - zi : zi;     // the slice this step crosses
     if (a.dn_stage && nrow > 0) {
       if (threadIdx.x == 0) {
         const unsigned bytes = (unsigned)((size_t)nrow * N * sizeof(__half));
@@ -1157,6 +1163,15 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_batch_kernel(BatchArgs b) {
     }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(b.err, 0, kDevErrNan);
+}
+
+// Phase conjugation of a field (time reversal of a monochromatic wave): E <- conj(E).
+__global__ void bpm_conj_kernel(float2* E, size_t M) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+    float2 e = E[i];
+    e.y = -e.y;
+    E[i] = e;
+  }
 }
 
 // Per-focus patches of an intensity window (PSF de-multiplexing): thread i

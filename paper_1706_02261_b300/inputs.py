@@ -103,6 +103,55 @@ def sphere_phantom_dn(shape, d: float, n_spheres: int, seed: int,
     return vol.astype(np.float16)
 
 
+def _gradient_noise(shape, d: float, cell_um: float, rng) -> np.ndarray:
+    """One octave of periodic gradient (Perlin) noise: unit gradient vectors on
+    a lattice of about ``cell_um`` spacing that tiles the box, the dot product
+    of each corner's gradient with the offset to the voxel, blended with the
+    quintic fade 6t^5 - 15t^4 + 10t^3 along each axis.  Values in about
+    [-1, 1]; computed slice by slice."""
+    nz, ny, nx = shape
+    L = [max(1, int(round(n * d / cell_um))) for n in (nx, ny, nz)]
+    g = rng.normal(size=(L[2], L[1], L[0], 3))
+    g /= np.linalg.norm(g, axis=-1, keepdims=True)
+    fade = lambda t: t * t * t * (t * (t * 6.0 - 15.0) + 10.0)
+    ux = np.arange(nx) * L[0] / nx
+    uy = np.arange(ny) * L[1] / ny
+    x0 = np.floor(ux).astype(int)
+    y0 = np.floor(uy).astype(int)
+    fx = (ux - x0)[None, :]
+    fy = (uy - y0)[:, None]
+    out = np.empty(shape, np.float32)
+    for z in range(nz):
+        uz = z * L[2] / nz
+        z0 = int(np.floor(uz))
+        fz = uz - z0
+        acc = np.zeros((ny, nx))
+        for cz in (0, 1):
+            wz = fade(fz) if cz else 1 - fade(fz)
+            for cy in (0, 1):
+                wy = fade(fy) if cy else 1 - fade(fy)
+                for cx in (0, 1):
+                    wx = fade(fx) if cx else 1 - fade(fx)
+                    gg = g[(z0 + cz) % L[2]][np.ix_((y0 + cy) % L[1], (x0 + cx) % L[0])]
+                    dot = gg[..., 0] * (fx - cx) + gg[..., 1] * (fy - cy) + gg[..., 2] * (fz - cz)
+                    acc += wz * wy * wx * dot
+        out[z] = acc
+    return out
+
+
+def perlin_phantom_dn(shape, d: float, seed: int, n_mean: float = 1.36, n_amp: float = 0.03,
+                      cell_um: float = 4.0, n0: float = N0) -> np.ndarray:
+    """Perlin-noise tissue of the paper's adaptive-optics example (n = 1.36 +-
+    0.03): two octaves of periodic gradient noise (cells of ``cell_um`` and
+    half of it, weights 1 and 1/2), scaled so its largest magnitude is 1, then
+    dn = n_mean - n0 + n_amp * noise, rounded to FP16.  Draws from
+    ``default_rng(seed)``.  Returns [nz][ny][nx] FP16."""
+    rng = np.random.default_rng(seed)
+    noise = _gradient_noise(shape, d, cell_um, rng) + 0.5 * _gradient_noise(shape, d, cell_um / 2, rng)
+    noise /= max(float(np.max(np.abs(noise))), 1e-30)
+    return (n_mean - n0 + n_amp * noise).astype(np.float16)
+
+
 # --------------------------------------------------------------------------
 # input fields and emitter lattices
 # --------------------------------------------------------------------------
