@@ -236,6 +236,16 @@ int bpm_propagate_host(bpm_plan_t p, const void *h_dn, const void *Ein, int ein_
 int bpm_multiplex_psf(bpm_plan_t p, int inst, int n_foci, const double *h_xyz,
                       const double *h_phase, double NA, void *d_Eout, cudaStream_t stream);
 
+/* bpm_multiplex_annular - bpm_multiplex_psf with the annular pupil
+ * NA_in <= |k_perp| / k0 <= NA_out: each emitter becomes a Bessel beam
+ * (propagation-invariant as the annulus narrows), and a row of emitters a
+ * Bessel lattice, one of the paper's illumination modalities (light-sheet
+ * modalities paragraph).  Unit energy per emitter; the pupil membership is
+ * decided in FP64 as for the disk.  NA_in = 0 is bpm_multiplex_psf.
+ * Errors: as bpm_multiplex_psf; BPM_ERR_ARG unless 0 <= NA_in < NA_out. */
+int bpm_multiplex_annular(bpm_plan_t p, int inst, int n_foci, const double *h_xyz, const double *h_phase,
+                          double NA_in, double NA_out, void *d_Eout, cudaStream_t stream);
+
 /* bpm_light_sheet - cylindrical light sheet (the paper's Fig. 2a illumination,
  * NA 0.15): thin along x, uniform along y; angular spectrum
  * exp(-(kx w0 / 2)^2) on the ky = 0 line, w0 = lambda / (pi NA), centred at

@@ -53,10 +53,13 @@ def _load():
         lib.oracle_propagator.argtypes = [i, i, d, d, d, d, d, p]
         lib.oracle_bpm.argtypes = [i, i, i, d, d, d, d, d, p, p, p, p]
         lib.oracle_bpm_adaptive.argtypes = [i, i, i, d, d, d, d, d, p, p, p, p]
+        lib.oracle_bpm_absorbing.argtypes = [i, i, i, d, d, d, d, d, p, p, p, p, p]
         lib.oracle_multiplex_psf.argtypes = [i, i, d, d, d, d, i, p, p, p, p, d, p]
+        lib.oracle_multiplex_annular.argtypes = [i, i, d, d, d, d, i, p, p, p, p, d, d, p]
         lib.oracle_light_sheet.argtypes = [i, i, d, d, d, d, d, d, p]
         for f in (lib.oracle_dft1, lib.oracle_dft2, lib.oracle_propagator, lib.oracle_bpm, lib.oracle_bpm_adaptive,
-                  lib.oracle_multiplex_psf, lib.oracle_light_sheet):
+                  lib.oracle_bpm_absorbing,
+                  lib.oracle_multiplex_psf, lib.oracle_multiplex_annular, lib.oracle_light_sheet):
             f.restype = i
         lib.oracle_num_threads.restype = i
         _lib = lib
@@ -103,13 +106,15 @@ def propagator(nx, ny, dx, dy, dz, lam, n0) -> np.ndarray:
     return H
 
 
-def bpm(dn, E0, dx, dy, dz, lam, n0, want_intensity: bool = True, adaptive: bool = False):
+def bpm(dn, E0, dx, dy, dz, lam, n0, want_intensity: bool = True, adaptive: bool = False, kappa=None):
     """Split-step BPM through every slice of ``dn`` ([nz][ny][nx], n - n0).
 
     Returns ``(E_out, I)`` where ``I`` is the [nz][ny][nx] volume of |E|^2 after
     each slice's screen (``None`` when ``want_intensity`` is false).  With
     ``adaptive`` the locally adapted expansion of reading B (per-slice mean
-    index as the reference, first-order corrected propagator) is used.
+    index as the reference, first-order corrected propagator) is used.  With
+    ``kappa`` (same shape as ``dn``) the index is complex, n0 + dn + i kappa,
+    and each screen also attenuates by exp(-k0 kappa dz).
     """
     dn = np.ascontiguousarray(dn, dtype=np.float64)
     nz, ny, nx = dn.shape
@@ -117,8 +122,15 @@ def bpm(dn, E0, dx, dy, dz, lam, n0, want_intensity: bool = True, adaptive: bool
     assert E0.shape == (ny, nx)
     Eout = np.zeros((ny, nx), np.complex128)
     I = np.zeros((nz, ny, nx), np.float64) if want_intensity else None
-    fn = _load().oracle_bpm_adaptive if adaptive else _load().oracle_bpm
-    rc = fn(nx, ny, nz, dx, dy, dz, lam, n0, _ptr(dn), _ptr(E0), _ptr(Eout), _ptr(I) if I is not None else None)
+    if kappa is not None:
+        assert not adaptive, "the oracle has no adapted expansion with absorption"
+        kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+        assert kappa.shape == dn.shape
+        rc = _load().oracle_bpm_absorbing(nx, ny, nz, dx, dy, dz, lam, n0, _ptr(dn), _ptr(kappa), _ptr(E0),
+                                          _ptr(Eout), _ptr(I) if I is not None else None)
+    else:
+        fn = _load().oracle_bpm_adaptive if adaptive else _load().oracle_bpm
+        rc = fn(nx, ny, nz, dx, dy, dz, lam, n0, _ptr(dn), _ptr(E0), _ptr(Eout), _ptr(I) if I is not None else None)
     _check(rc, "bpm")
     return Eout, I
 
@@ -134,6 +146,20 @@ def multiplex_psf(nx, ny, dx, dy, lam, n0, ix, iy, phase, zf, NA) -> np.ndarray:
     rc = _load().oracle_multiplex_psf(nx, ny, dx, dy, lam, n0, ix.size, _ptr(ix), _ptr(iy),
                                       _ptr(phase), _ptr(zf), NA, _ptr(E))
     _check(rc, "multiplex_psf")
+    return E
+
+
+def multiplex_annular(nx, ny, dx, dy, lam, n0, ix, iy, phase, zf, NA_in, NA_out) -> np.ndarray:
+    """As multiplex_psf with the annular pupil NA_in <= |k_perp|/k0 <= NA_out
+    (Bessel beams; several emitters give a Bessel lattice)."""
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    phase = np.ascontiguousarray(phase, dtype=np.float64)
+    zf = np.ascontiguousarray(np.broadcast_to(zf, ix.shape), dtype=np.float64)
+    E = np.zeros((ny, nx), np.complex128)
+    rc = _load().oracle_multiplex_annular(nx, ny, dx, dy, lam, n0, ix.size, _ptr(ix), _ptr(iy),
+                                          _ptr(phase), _ptr(zf), NA_in, NA_out, _ptr(E))
+    _check(rc, "multiplex_annular")
     return E
 
 

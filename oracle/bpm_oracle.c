@@ -184,6 +184,44 @@ int oracle_propagator(int nx, int ny, double dx, double dy, double dz,
     return 0;
 }
 
+/* Complex refractive index n = n0 + dn + i kappa (absorption for kappa > 0):
+ * the same loop with the screen exp(i k0 (dn + i kappa) dz), i.e. the phase
+ * exp(i k0 dn dz) times the attenuation exp(-k0 kappa dz).  kappa: [nz][ny][nx]
+ * doubles; other arguments as oracle_bpm. */
+int oracle_bpm_absorbing(int nx, int ny, int nz, double dx, double dy, double dz,
+                         double lambda, double n0, const double *dn, const double *kappa,
+                         const double *E0v, double *Eoutv, double *Iout)
+{
+    if (nx < 1 || ny < 1 || nz < 0 || !(dz > 0)) return -1;
+    size_t M = (size_t)nx * ny;
+    cplx *H = (cplx *)malloc(sizeof(cplx) * M);
+    cplx *E = (cplx *)malloc(sizeof(cplx) * M);
+    if (oracle_propagator(nx, ny, dx, dy, dz, lambda, n0, (double *)H) != 0) {
+        free(H);
+        free(E);
+        return -1;
+    }
+    memcpy(E, E0v, sizeof(cplx) * M);
+    double k0 = kTwoPi / lambda;
+    for (int z = 0; z < nz; ++z) {
+        oracle_dft2(nx, ny, (double *)E, -1);
+        for (size_t i = 0; i < M; ++i) E[i] *= H[i];
+        oracle_dft2(nx, ny, (double *)E, +1);
+        const double *d_re = dn + (size_t)z * M, *d_im = kappa + (size_t)z * M;
+#pragma omp parallel for schedule(static)
+        for (long long i = 0; i < (long long)M; ++i) {
+            cplx e = E[i] / (double)M;
+            e *= cexp(I * k0 * d_re[i] * dz) * exp(-k0 * d_im[i] * dz);
+            E[i] = e;
+            if (Iout) Iout[(size_t)z * M + (size_t)i] = creal(e) * creal(e) + cimag(e) * cimag(e);
+        }
+    }
+    memcpy(Eoutv, E, sizeof(cplx) * M);
+    free(H);
+    free(E);
+    return 0;
+}
+
 /* Reading B of the locally adapted expansion (see the header): per slice the
  * mean index step delta_z, the propagator corrected to first order in
  * delta_z, and the screen of dn - delta_z.  Arguments as oracle_bpm. */
@@ -280,21 +318,23 @@ int oracle_bpm(int nx, int ny, int nz, double dx, double dy, double dz,
  * sum |E|^2 = 1 before the foci are summed.  Foci at different depths are
  * synthesised one at a time and added.
  *   Eout : [ny][nx] complex, overwritten. */
-int oracle_multiplex_psf(int nx, int ny, double dx, double dy, double lambda, double n0,
-                         int n_foci, const int *ix, const int *iy, const double *phase,
-                         const double *zf, double NA, double *Eoutv)
+/* Multiplexed focused emitters through the pupil NA_in <= |k_perp| / k0 <= NA
+ * (a disk for NA_in = 0, the Bessel-beam annulus otherwise). */
+static int multiplex_pupil(int nx, int ny, double dx, double dy, double lambda, double n0,
+                           int n_foci, const int *ix, const int *iy, const double *phase,
+                           const double *zf, double NA_in, double NA, double *Eoutv)
 {
-    if (nx < 1 || ny < 1 || n_foci < 0 || !(NA > 0)) return -1;
+    if (nx < 1 || ny < 1 || n_foci < 0 || !(NA > 0) || !(NA_in >= 0) || !(NA_in < NA)) return -1;
     size_t M = (size_t)nx * ny;
     cplx *Eout = (cplx *)Eoutv;
     cplx *F = (cplx *)malloc(sizeof(cplx) * M);
-    double k0 = kTwoPi / lambda, K = k0 * n0, kna = k0 * NA;
+    double k0 = kTwoPi / lambda, K = k0 * n0, kna = k0 * NA, kin = k0 * NA_in;
     long long n_pupil = 0;
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double kx = grid_k(x, nx, dx), ky = grid_k(y, ny, dy);
             double kp2 = kx * kx + ky * ky;
-            if (kp2 <= kna * kna && K * K - kp2 > 0) ++n_pupil;
+            if (kp2 >= kin * kin && kp2 <= kna * kna && K * K - kp2 > 0) ++n_pupil;
         }
     for (size_t i = 0; i < M; ++i) Eout[i] = 0;
     if (n_pupil == 0 || n_foci == 0) {
@@ -319,7 +359,7 @@ int oracle_multiplex_psf(int nx, int ny, double dx, double dy, double lambda, do
                 double kx = grid_k(x, nx, dx), ky = grid_k(y, ny, dy);
                 double kp2 = kx * kx + ky * ky, kz2 = K * K - kp2;
                 size_t i = (size_t)y * nx + x;
-                if (kp2 <= kna * kna && kz2 > 0)
+                if (kp2 >= kin * kin && kp2 <= kna * kna && kz2 > 0)
                     F[i] *= cexp(-I * sqrt(kz2) * zg);
                 else
                     F[i] = 0;
@@ -330,6 +370,22 @@ int oracle_multiplex_psf(int nx, int ny, double dx, double dy, double lambda, do
     free(done);
     free(F);
     return 0;
+}
+
+int oracle_multiplex_psf(int nx, int ny, double dx, double dy, double lambda, double n0,
+                         int n_foci, const int *ix, const int *iy, const double *phase,
+                         const double *zf, double NA, double *Eoutv)
+{
+    return multiplex_pupil(nx, ny, dx, dy, lambda, n0, n_foci, ix, iy, phase, zf, 0.0, NA, Eoutv);
+}
+
+/* Bessel beams (and lattices of them, several emitters): the annular pupil
+ * NA_in <= |k_perp| / k0 <= NA_out.  Arguments as oracle_multiplex_psf. */
+int oracle_multiplex_annular(int nx, int ny, double dx, double dy, double lambda, double n0,
+                             int n_foci, const int *ix, const int *iy, const double *phase,
+                             const double *zf, double NA_in, double NA_out, double *Eoutv)
+{
+    return multiplex_pupil(nx, ny, dx, dy, lambda, n0, n_foci, ix, iy, phase, zf, NA_in, NA_out, Eoutv);
 }
 
 /* Cylindrical light sheet, thin along x and uniform along y: angular spectrum

@@ -57,6 +57,7 @@ _pp = ctypes.POINTER(ctypes.c_void_p)
 _lib.bpm_plan.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(bpm_instance_desc), _i, _u, _vp]
 _lib.bpm_propagate.argtypes = [_vp, _pp, _pp, _pp, _pp, _i, _i, _vp]
 _lib.bpm_multiplex_psf.argtypes = [_vp, _i, _i, _vp, _vp, _d, _vp, _vp]
+_lib.bpm_multiplex_annular.argtypes = [_vp, _i, _i, _vp, _vp, _d, _d, _vp, _vp]
 _lib.bpm_light_sheet.argtypes = [_vp, _i, _d, _d, _vp, _vp]
 _lib.bpm_check.argtypes = [_vp]
 _lib.bpm_free.argtypes = [_vp]
@@ -227,6 +228,17 @@ def bpm_multiplex_psf(plan, inst: int, xyz: np.ndarray, phase: np.ndarray, NA: f
     return _check(_lib.bpm_multiplex_psf(plan, inst, phase.size, ctypes.c_void_p(xyz.ctypes.data),
                                          ctypes.c_void_p(phase.ctypes.data), NA, _ptr(e_out),
                                          _stream_handle(stream)))
+
+
+def bpm_multiplex_annular(plan, inst: int, xyz: np.ndarray, phase: np.ndarray, NA_in: float, NA_out: float, e_out,
+                          stream=None) -> int:
+    """Bessel beams / lattices: emitters through the annulus NA_in <= |k_perp|/k0 <= NA_out."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    phase = np.ascontiguousarray(phase, dtype=np.float64).reshape(-1)
+    assert phase.size == xyz.shape[0]
+    return _check(_lib.bpm_multiplex_annular(plan, inst, phase.size, ctypes.c_void_p(xyz.ctypes.data),
+                                             ctypes.c_void_p(phase.ctypes.data), NA_in, NA_out, _ptr(e_out),
+                                             _stream_handle(stream)))
 
 
 def bpm_light_sheet(plan, inst: int, NA: float, zf: float, e_out, stream=None) -> int:

@@ -727,13 +727,16 @@ extern "C" int bpm_demultiplex(bpm_plan_t p, int inst, const float* d_I, int w_b
   return finish_call(p, stream);
 }
 
-extern "C" int bpm_multiplex_psf(bpm_plan_t p, int inst, int n_foci, const double* h_xyz, const double* h_phase,
-                                 double NA, void* d_Eout, cudaStream_t stream) {
+namespace {
+
+int multiplex_impl(bpm_plan_t p, int inst, int n_foci, const double* h_xyz, const double* h_phase, double NA_in,
+                   double NA, void* d_Eout, cudaStream_t stream) {
   if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
   if (inst < 0 || inst >= (int)p->inst.size()) return fail(BPM_ERR_ARG, "instance %d out of range", inst);
   if (n_foci < 0 || n_foci > (1 << 20)) return fail(BPM_ERR_ARG, "n_foci must be in [0, 1048576]");
   if (n_foci > 0 && (!h_xyz || !h_phase)) return fail(BPM_ERR_ARG, "h_xyz and h_phase must be non-NULL");
   if (!(NA > 0) || !std::isfinite(NA)) return fail(BPM_ERR_ARG, "NA must be positive");
+  if (!(NA_in >= 0) || !(NA_in < NA)) return fail(BPM_ERR_ARG, "need 0 <= NA_in < NA");
   if (!d_Eout) return fail(BPM_ERR_ARG, "d_Eout is NULL");
   if (!aligned16(d_Eout)) return fail(BPM_ERR_ALIGN, "d_Eout must be 16-byte aligned");
   const InstPlan& in = p->inst[inst];
@@ -783,11 +786,13 @@ extern "C" int bpm_multiplex_psf(bpm_plan_t p, int inst, int n_foci, const doubl
   BPM_CU(cudaMemcpyAsync(p->foci_phase, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice, stream));
   const double k0 = kTwoPi / in.d.lambda;
   const double kna = k0 * NA;
+  const double kin = k0 * NA_in;
   StepArgs a = base_args(p, in, r);
   a.kna2 = kna * kna;
+  a.kin2 = kin * kin;
   BPM_CU(cudaMemsetAsync(p->npupil, 0, sizeof(unsigned long long), stream));
-  bpm_pupil_count_kernel<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>(n, in.d.dx, in.d.dy, a.k0n0, a.kna2,
-                                                                         p->npupil);
+  bpm_pupil_count_kernel<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>(n, in.d.dx, in.d.dy, a.k0n0, a.kin2,
+                                                                         a.kna2, p->npupil);
   BPM_CU(cudaGetLastError());
   size_t g0 = 0;
   int group = 0;
@@ -810,6 +815,19 @@ extern "C" int bpm_multiplex_psf(bpm_plan_t p, int inst, int n_foci, const doubl
     ++group;
   }
   return finish_call(p, stream);
+}
+
+}  // namespace
+
+extern "C" int bpm_multiplex_psf(bpm_plan_t p, int inst, int n_foci, const double* h_xyz, const double* h_phase,
+                                 double NA, void* d_Eout, cudaStream_t stream) {
+  return multiplex_impl(p, inst, n_foci, h_xyz, h_phase, 0.0, NA, d_Eout, stream);
+}
+
+extern "C" int bpm_multiplex_annular(bpm_plan_t p, int inst, int n_foci, const double* h_xyz,
+                                     const double* h_phase, double NA_in, double NA_out, void* d_Eout,
+                                     cudaStream_t stream) {
+  return multiplex_impl(p, inst, n_foci, h_xyz, h_phase, NA_in, NA_out, d_Eout, stream);
 }
 
 extern "C" int bpm_light_sheet(bpm_plan_t p, int inst, double NA, double zf, void* d_Eout, cudaStream_t stream) {

@@ -272,6 +272,7 @@ struct StepArgs {
   int z_begin, z_end;
   // focusing filter (synthesis): multiplier exp(-i kz zf) / (n n) inside the pupil
   double k0n0, kna2, zf, dx, dy;   // k0 n0, (k0 NA)^2, focal depth, lateral spacings
+  double kin2;                     // (k0 NA_in)^2: inner edge of an annular pupil (0 for a disk)
   int accumulate;                  // INV_ACC: add into out instead of storing
   float2* out;                     // INV_ACC destination
   // team barrier
@@ -700,7 +701,7 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
           const double kp2 = __dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky));
           const double kz2 = __dsub_rn(__dmul_rn(a.k0n0, a.k0n0), kp2);
           float2 m = make_float2(0.f, 0.f);
-          if (kp2 <= a.kna2 && kz2 > 0.0) {
+          if (kp2 >= a.kin2 && kp2 <= a.kna2 && kz2 > 0.0) {
             double ph = -sqrt(kz2) * a.zf;
             ph -= 6.283185307179586 * rint(ph * 0.15915494309189535);
             float sn, cs;
@@ -1000,8 +1001,8 @@ __global__ void bpm_scatter_kernel(float2* field, int n, const int* idx, const d
   atomicAdd(p + 1, (float)(amp * sn));
 }
 
-// Count DFT bins inside the pupil |k_perp|^2 <= kna2 that also propagate.
-__global__ void bpm_pupil_count_kernel(int n, double dx, double dy, double k0n0, double kna2,
+// Count DFT bins inside the pupil kin2 <= |k_perp|^2 <= kna2 that also propagate.
+__global__ void bpm_pupil_count_kernel(int n, double dx, double dy, double k0n0, double kin2, double kna2,
                                        unsigned long long* count) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   unsigned long long c = 0;
@@ -1012,7 +1013,7 @@ __global__ void bpm_pupil_count_kernel(int n, double dx, double dy, double k0n0,
     const double ky = __ddiv_rn(__dmul_rn(6.283185307179586, (double)fy), __dmul_rn((double)n, dy));
     const double kp2 = __dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky));
     const double kz2 = __dsub_rn(__dmul_rn(k0n0, k0n0), kp2);
-    c = (kp2 <= kna2 && kz2 > 0.0) ? 1ull : 0ull;
+    c = (kp2 >= kin2 && kp2 <= kna2 && kz2 > 0.0) ? 1ull : 0ull;
   }
   // warp reduce, one atomic per warp
   for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);

@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import tests.test_oracle_adaptive as t_ada
+import tests.test_oracle_absorption as t_abs
 import tests.test_oracle_fft as t_fft
 import tests.test_oracle_propagation as t_prop
 import tests.test_oracle_synthesis as t_syn
@@ -32,11 +33,16 @@ MUTATIONS = [
      "acc += t[a] * root_of_unity((long long)a * (k + (long long)b * m), n, -sign);"),
     ("emitter amplitude", "double amp = sqrt((double)M / (double)n_pupil);", "double amp = sqrt((double)n_pupil / (double)M);"),
     ("defocus sign", "F[i] *= cexp(-I * sqrt(kz2) * zg);", "F[i] *= cexp(I * sqrt(kz2) * zg);"),
-    ("pupil radius from K", "if (kp2 <= kna * kna && K * K - kp2 > 0) ++n_pupil;", "if (kp2 <= K * K && K * K - kp2 > 0) ++n_pupil;"),
+    ("pupil radius from K", "if (kp2 >= kin * kin && kp2 <= kna * kna && K * K - kp2 > 0) ++n_pupil;",
+     "if (kp2 >= kin * kin && kp2 <= K * K && K * K - kp2 > 0) ++n_pupil;"),
     ("light-sheet waist", "w0 = lambda / (M_PI * NA);", "w0 = lambda / (2 * M_PI * NA);"),
     ("light-sheet centre", "double xc = (double)(nx / 2) * dx;", "double xc = (double)(nx / 2 + 1) * dx;"),
     ("adapted propagator correction sign", "cexp(I * (kz + delta * k0 * k0 * n0 / kz) * dz)",
      "cexp(I * (kz - delta * k0 * k0 * n0 / kz) * dz)"),
+    ("absorption sign", "e *= cexp(I * k0 * d_re[i] * dz) * exp(-k0 * d_im[i] * dz);",
+     "e *= cexp(I * k0 * d_re[i] * dz) * exp(k0 * d_im[i] * dz);"),
+    ("absorption on the amplitude squared", "e *= cexp(I * k0 * d_re[i] * dz) * exp(-k0 * d_im[i] * dz);",
+     "e *= cexp(I * k0 * d_re[i] * dz) * exp(-2 * k0 * d_im[i] * dz);"),
     ("adapted screen keeps the mean", "e *= cexp(I * k0 * (slice[i] - delta) * dz);", "e *= cexp(I * k0 * slice[i] * dz);"),
 ]
 
@@ -48,6 +54,7 @@ PINS = [
     t_syn.test_each_focus_has_unit_energy, t_syn.test_single_focus_forms_at_its_depth_and_position,
     t_syn.test_light_sheet_focus_profile, t_ada.test_zero_mean_slices_give_reading_a,
     t_ada.test_uniform_slices_tilted_plane_wave_closed_forms, t_ada.test_reading_b_beats_reading_a_in_a_uniform_medium,
+    t_abs.test_zero_kappa_is_the_lossless_method, t_abs.test_uniform_kappa_follows_beer_lambert,
 ]
 
 
@@ -76,7 +83,7 @@ def test_pins_catch_mutation(tmp_path, monkeypatch, tag, find, repl):
     mod = _mutated_oracle(tmp_path, find, repl, tag)
     failed = []
     for pin in PINS:
-        for m in (t_fft, t_prop, t_syn, t_ada):
+        for m in (t_fft, t_prop, t_syn, t_ada, t_abs):
             monkeypatch.setattr(m, "oracle", mod)
         try:
             if pin is t_fft.test_dft_matches_numpy:
