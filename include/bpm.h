@@ -148,6 +148,17 @@ int bpm_propagate_window(bpm_plan_t p, const void *const *d_dn, const void *cons
 int bpm_propagate_reverse(bpm_plan_t p, const void *d_dn, const void *d_Ein, void *d_Eout, float *d_I,
                           int z_begin, int z_end, cudaStream_t stream);
 
+/* bpm_propagate_absorbing - bpm_propagate of a single-instance plan with a
+ * complex refractive index n = n0 + dn + i kappa (the paper's phantoms may
+ * absorb: adaptive-optics paragraph): each slice's screen is
+ * exp(i k0 (dn + i kappa) dz) = exp(i k0 dn dz) exp(-k0 kappa dz).
+ *   d_kappa : device FP16 volume [nz][ny][nx] of kappa (>= 0 absorbs), 16-byte
+ *             aligned; each value read once (global streaming loads)
+ * Other arguments as bpm_propagate.  Errors: as bpm_propagate;
+ * BPM_ERR_UNSUPPORTED for batched plans and with BPM_FLAG_ADAPTIVE. */
+int bpm_propagate_absorbing(bpm_plan_t p, const void *d_dn, const void *d_kappa, const void *d_Ein,
+                            void *d_Eout, float *d_I, int z_begin, int z_end, cudaStream_t stream);
+
 /* bpm_phase_conjugate - E <- conj(E) in place on instance inst's field (the
  * time-reversed monochromatic wave).  d_E: device complex float [ny][nx],
  * 16-byte aligned.  Errors: BPM_ERR_ARG, BPM_ERR_ALIGN, BPM_ERR_CUDA. */

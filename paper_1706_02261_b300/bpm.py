@@ -70,6 +70,7 @@ _lib.bpm_propagate_static.argtypes = [ctypes.POINTER(bpm_instance_desc), _vp, _v
 _lib.bpm_propagate_window.argtypes = [_vp, _pp, _pp, _pp, _pp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), _vp]
 _lib.bpm_propagate_reverse.argtypes = [_vp, _vp, _vp, _vp, _vp, _i, _i, _vp]
 _lib.bpm_phase_conjugate.argtypes = [_vp, _i, _vp, _vp]
+_lib.bpm_propagate_absorbing.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp]
 _lib.bpm_demultiplex.argtypes = [_vp, _i, _vp, _i, _i, _i, ctypes.POINTER(_i), _i, _i, _i, _vp, _vp]
 for _f in ("bpm_plan", "bpm_propagate", "bpm_multiplex_psf", "bpm_light_sheet", "bpm_check",
            "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout", "bpm_propagate_static", "bpm_autotune", "bpm_propagate_host"):
@@ -179,6 +180,13 @@ def bpm_propagate_reverse(plan, dn, e_in, e_out, inten=None, z_begin: int = 0, z
     """Slices z_end-1 down to z_begin (propagation towards -z), single-instance plans."""
     return _check(_lib.bpm_propagate_reverse(plan, _ptr(dn), _ptr(e_in), _ptr(e_out), _ptr(inten), z_begin, z_end,
                                              _stream_handle(stream)))
+
+
+def bpm_propagate_absorbing(plan, dn, kappa, e_in, e_out, inten=None, z_begin: int = 0, z_end: int = 2 ** 31 - 1,
+                            stream=None) -> int:
+    """Complex index n0 + dn + i kappa (FP16 volumes), single-instance plans."""
+    return _check(_lib.bpm_propagate_absorbing(plan, _ptr(dn), _ptr(kappa), _ptr(e_in), _ptr(e_out), _ptr(inten),
+                                               z_begin, z_end, _stream_handle(stream)))
 
 
 def bpm_phase_conjugate(plan, inst: int, e, stream=None) -> int:

@@ -178,6 +178,8 @@ int setup_kernels(NRes& r, int sms) {
   BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_STEP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_LAST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_INV_ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   BPM_CU(cudaFuncSetAttribute(bpm_col_kernel<N, COL_PROP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   BPM_CU(cudaFuncSetAttribute(bpm_col_kernel<N, COL_FOCUS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -205,6 +207,8 @@ int setup_kernels(NRes& r, int sms) {
   if (r.smem + db > budget) r.dn_stage = 0;
   r.smem_persist = r.smem + (r.h_res ? hb : 0) + (r.dn_stage ? db : 0) + (r.i_stage ? ib : 0);
   BPM_CU(cudaFuncSetAttribute(bpm_persistent_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)r.smem_persist));
+  BPM_CU(cudaFuncSetAttribute((bpm_persistent_kernel<N, true>), cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)r.smem_persist));
   int per_sm = 0;
   BPM_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpm_persistent_kernel<N>, kThreads,
@@ -313,16 +317,22 @@ int launch_propagate(bpm_plan_s* p, const NRes& r, StepArgs a, cudaStream_t s) {
     for (int zi = a.z_begin; zi < a.z_end; ++zi) {
       const int z = a.reverse ? a.z_begin + a.z_end - 1 - zi : zi;     // slice crossed by this step
       bpm_col_kernel<N, COL_PROP><<<G, kThreads, r.smem, s>>>(a, z);
-      if (zi + 1 < a.z_end) bpm_row_kernel<N, ROW_STEP><<<G, kThreads, r.smem, s>>>(a, z);
-      else bpm_row_kernel<N, ROW_LAST><<<G, kThreads, r.smem, s>>>(a, z);
+      const bool last = zi + 1 == a.z_end;
+      if (a.kappa) {
+        if (!last) bpm_row_kernel<N, ROW_STEP, true><<<G, kThreads, r.smem, s>>>(a, z);
+        else bpm_row_kernel<N, ROW_LAST, true><<<G, kThreads, r.smem, s>>>(a, z);
+      } else {
+        if (!last) bpm_row_kernel<N, ROW_STEP><<<G, kThreads, r.smem, s>>>(a, z);
+        else bpm_row_kernel<N, ROW_LAST><<<G, kThreads, r.smem, s>>>(a, z);
+      }
     }
     BPM_CU(cudaGetLastError());
     return BPM_OK;
   }
   BPM_CU(cudaMemsetAsync(p->bar, 0, sizeof(unsigned), s));
   void* args[] = {&a};
-  BPM_CU(cudaLaunchCooperativeKernel((const void*)bpm_persistent_kernel<N>, dim3(G), dim3(kThreads), args,
-                                     r.smem_persist, s));
+  const void* fn = a.kappa ? (const void*)bpm_persistent_kernel<N, true> : (const void*)bpm_persistent_kernel<N>;
+  BPM_CU(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args, r.smem_persist, s));
   return BPM_OK;
 }
 
@@ -597,7 +607,7 @@ namespace {
 
 int propagate_impl(bpm_plan_t p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
                    float* const* d_I, int z_begin, int z_end, const int* w_begin, const int* w_end,
-                   cudaStream_t stream, bool reverse = false) {
+                   cudaStream_t stream, bool reverse = false, const void* d_kappa = nullptr) {
   if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
   if (!d_dn || !d_Ein || !d_Eout) return fail(BPM_ERR_ARG, "d_dn, d_Ein and d_Eout must be non-NULL arrays");
   if (z_begin < 0 || z_end < z_begin) return fail(BPM_ERR_ARG, "need 0 <= z_begin <= z_end");
@@ -615,6 +625,10 @@ int propagate_impl(bpm_plan_t p, const void* const* d_dn, const void* const* d_E
       return fail(BPM_ERR_ALIGN, "instance %zu: device pointers must be 16-byte aligned", i);
   }
   if (reverse && p->inst.size() > 1) return fail(BPM_ERR_UNSUPPORTED, "reverse propagation takes single-instance plans");
+  if (d_kappa && (p->inst.size() > 1 || reverse || (p->flags & BPM_FLAG_ADAPTIVE)))
+    return fail(BPM_ERR_UNSUPPORTED, "absorption takes forward propagations of single-instance plans without "
+                                     "BPM_FLAG_ADAPTIVE");
+  if (d_kappa && !aligned16(d_kappa)) return fail(BPM_ERR_ALIGN, "d_kappa must be 16-byte aligned");
   if (p->inst.size() > 1) {
     int rc = propagate_batch(p, d_dn, d_Ein, d_Eout, d_I, z_begin, z_end, w_begin, w_end, stream);
     if (rc) return rc;
@@ -640,6 +654,7 @@ int propagate_impl(bpm_plan_t p, const void* const* d_dn, const void* const* d_E
     a.z_begin = zb;
     a.z_end = ze;
     a.reverse = reverse ? 1 : 0;
+    a.kappa = static_cast<const __half*>(d_kappa);
     if (in.delta) {
       // reading B: mean index step of slices [zb, ze) before the propagation
       // (delta is indexed by absolute slice, as dn is)
@@ -679,6 +694,17 @@ extern "C" int bpm_propagate_reverse(bpm_plan_t p, const void* d_dn, const void*
   void* eout[1] = {d_Eout};
   float* inten[1] = {d_I};
   return propagate_impl(p, dn, ein, eout, d_I ? inten : nullptr, z_begin, z_end, nullptr, nullptr, stream, true);
+}
+
+extern "C" int bpm_propagate_absorbing(bpm_plan_t p, const void* d_dn, const void* d_kappa, const void* d_Ein,
+                                       void* d_Eout, float* d_I, int z_begin, int z_end, cudaStream_t stream) {
+  if (!d_kappa) return fail(BPM_ERR_ARG, "d_kappa is NULL");
+  const void* dn[1] = {d_dn};
+  const void* ein[1] = {d_Ein};
+  void* eout[1] = {d_Eout};
+  float* inten[1] = {d_I};
+  return propagate_impl(p, dn, ein, eout, d_I ? inten : nullptr, z_begin, z_end, nullptr, nullptr, stream, false,
+                        d_kappa);
 }
 
 extern "C" int bpm_phase_conjugate(bpm_plan_t p, int inst, void* d_E, cudaStream_t stream) {

@@ -265,6 +265,9 @@ struct StepArgs {
   // (index, slice mean and intensity of that slice); the field enters at the
   // exit plane of slice z_end - 1
   int reverse;
+  // complex index (absorption): imaginary part kappa of n per voxel,
+  // [nz][n][n] FP16, or nullptr; the screen attenuates by exp(-k0 kappa dz)
+  const __half* kappa;
   const float2* ht;        // [n][n] propagator, transposed: ht[kx * n + ky]
   const float2* tw;        // twiddles: forward table then inverse table
   float screen_c;          // k0 dz
@@ -440,7 +443,7 @@ __device__ __forceinline__ void store_layout(const float2* v, float2* dst, int t
 // Rows [r0, r1) of the team member; each group of T threads takes one row per
 // round.  Groups without a row run the transforms on zeros (so that the warp
 // stays converged for __syncwarp) and skip all memory traffic.
-template <int N, int MODE>
+template <int N, int MODE, bool KAPPA = false>
 __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1, int z, float2* s_buf,
                                               const float2* s_twf, const float2* s_twi, bool& bad,
                                               const Stage& st = Stage()) {
@@ -492,6 +495,12 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
         for (int q = 0; q < C::PTS; ++q) dv[q] = __ldcs(dnrow + layout_index<N, C::T, C::R0>(q, t));
       }
       const __half* sdn = st.dn ? st.dn + (size_t)((active ? row : r0) - r0) * N : nullptr;
+      // absorption row (global memory, read once per element with streaming
+      // loads), only in the KAPPA instantiation: staging it next to the index
+      // rows would move the persistent kernel to the next, larger
+      // shared-memory carve-out and shrink L1, which slows the lossless path
+      const __half* skap = nullptr;
+      if constexpr (KAPPA) skap = a.kappa + ((size_t)z * N + (active ? row : r0)) * N;
       float* irow = nullptr;
       if (active && a.inten && z >= a.iz0 && z < a.iz1)
         irow = st.inten ? st.inten + (size_t)(row - r0) * N : a.inten + ((size_t)(z - a.iz0) * N + row) * N;
@@ -529,9 +538,29 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
             }
           }
         };
-        if (range == 0) body([](float ph) { return unit_phasor_small(ph); });
-        else if (range == 1) body([](float ph) { return unit_phasor_poly(ph); });
-        else body([](float ph) { return unit_phasor_libm(ph); });
+        if constexpr (KAPPA) {
+          // complex index: exp(i k0 (dn + i kappa) dz) = exp(i k0 dn dz) exp(-k0 kappa dz)
+          float ksum = 0.f;
+#pragma unroll
+          for (int q = 0; q < C::PTS; ++q) {
+            const int x = layout_index<N, C::T, C::R0>(q, t);
+            const float kv = __half2float(__ldcs(skap + x));
+            ksum += kv;
+            const float2 e = cmul(w[q], unit_phasor_reduced(fmaf(a.screen_c, dval[q], c0)));
+            const float att = expf(-a.screen_c * kv);
+            w[q] = make_float2(e.x * att, e.y * att);
+            if (irow) {
+              const float iv = fmaf(w[q].x, w[q].x, w[q].y * w[q].y);
+              if (i_smem) irow[x] = iv;
+              else __stcs(irow + x, iv);
+            }
+          }
+          bad |= active && !isfinite(ksum);
+        } else {
+          if (range == 0) body([](float ph) { return unit_phasor_small(ph); });
+          else if (range == 1) body([](float ph) { return unit_phasor_poly(ph); });
+          else body([](float ph) { return unit_phasor_libm(ph); });
+        }
       };
       if constexpr (MODE == ROW_LAST) {
         C::inv(v, buf, s_twf, s_twi, t);
@@ -805,7 +834,7 @@ __global__ void bpm_build_gt_kernel(float* gt, int nx, int ny, double dx, double
 // column half-step of slice z starts, so the HBM read overlaps it; the
 // intensity rows are written to shared memory by the row half-step and sent
 // to HBM by one bulk store that overlaps the next column half-step.
-template <int N>
+template <int N, bool KAPPA = false>
 __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a) {
   using C = Cfg<N>;
   extern __shared__ float4 smem_f4[];
@@ -834,6 +863,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
       st.dn = reinterpret_cast<const __half*>(s_extra + off);
       off += ((size_t)a.rmax * N * sizeof(__half) + 15) & ~(size_t)15;
     }
+
     if (a.i_stage && a.inten) st.inten = reinterpret_cast<float*>(s_extra + off);
   }
   if (a.h_res) {
@@ -868,8 +898,8 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
     }
     if (st.inten && threadIdx.x == 0) bulk_wait_reads();   // previous intensity store has read its rows
     if (__syncthreads_or(!ok)) break;
-    if (!last) row_half_step<N, ROW_STEP>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
-    else row_half_step<N, ROW_LAST>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
+    if (!last) row_half_step<N, ROW_STEP, KAPPA>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
+    else row_half_step<N, ROW_LAST, KAPPA>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
     if (st.inten && z >= a.iz0 && z < a.iz1) {
       fence_proxy_async_smem();
       __syncthreads();
@@ -887,7 +917,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
 }
 
 // One half-step per launch (comparison path and input synthesis).
-template <int N, int MODE>
+template <int N, int MODE, bool KAPPA = false>
 __global__ void __launch_bounds__(kThreads, 1) bpm_row_kernel(StepArgs a, int z) {
   using C = Cfg<N>;
   extern __shared__ float4 smem_f4[];
@@ -898,7 +928,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_row_kernel(StepArgs a, int z)
   const int G = gridDim.x, rank = blockIdx.x;
   const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
   bool bad = false;
-  row_half_step<N, MODE>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+  row_half_step<N, MODE, KAPPA>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
   if constexpr (MODE == ROW_STEP || MODE == ROW_LAST) report_bad(a, bad);
 }
 
