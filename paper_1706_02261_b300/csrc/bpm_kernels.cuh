@@ -141,19 +141,21 @@ struct GroupCfg : CfgBase<N_, T_, GS_> {
 // propagator multiply and the inverse (by conjugation) follow in registers.
 // Global loads and stores go straight to registers: per warp instruction,
 // rows a .. a + 32/NG - 1 of NG adjacent columns (64-byte segments at
-// N1 = 32).  Strides: a row of the block SA = 1 (mod 16) float2 and a column
-// block SC = 32 / NG (mod 16), so that both the row writes and the column
-// reads of a warp fall on distinct bank pairs; the staged propagator columns
-// use the row stride HS = N + 32 / NG for the same reason.
+// N1 = 32).  A 64-bit shared-memory access is served per half-warp, whose 16
+// lanes hold NG columns c and 16/NG rows a, so the strides make c SC + a SA
+// distinct modulo 16 float2 (16 bank pairs): a row of the block SA = 1 and a
+// column block SC = 16 / NG (mod 16) for both the row writes and the column
+// reads; the staged propagator columns use the row stride HS = N + 16 / NG.
 template <class Base, int N1>
 struct FourStepCfg : Base {
-  static_assert(N1 * N1 == Base::N && N1 * Base::NG == kThreads, "four-step layout needs N = N1^2, N1 NG = kThreads");
+  static_assert(N1 * N1 == Base::N && N1 * Base::NG == kThreads && Base::NG <= 16,
+                "four-step layout needs N = N1^2, N1 NG = kThreads, NG <= 16");
   static constexpr int FS_N1 = N1;
   static constexpr int FS_SA = (N1 + 15) / 16 * 16 + 1;
-  static constexpr int FS_SC = N1 * FS_SA + ((32 / Base::NG) % 16 - (N1 * FS_SA) % 16 + 16) % 16;
+  static constexpr int FS_SC = N1 * FS_SA + ((16 / Base::NG) % 16 - (N1 * FS_SA) % 16 + 16) % 16;
   static constexpr int TW4 = Base::N;       // W_N^(a k) at [k N1 + a]
   static constexpr int BUFLEN = Base::NG * FS_SC > Base::NG * Base::GS ? Base::NG * FS_SC : Base::NG * Base::GS;
-  static constexpr int HS = Base::N + 32 / Base::NG;
+  static constexpr int HS = Base::N + 16 / Base::NG;
 };
 
 using Rad8x16 = Radices<8, 16>;
