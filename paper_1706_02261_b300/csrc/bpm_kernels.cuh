@@ -531,13 +531,15 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
 #pragma unroll
           for (int q = 0; q < C::PTS; ++q) {
             const int x = layout_index<N, C::T, C::R0>(q, t);
-            const float2 e = cmul(w[q], phasor(fmaf(a.screen_c, dval[q], c0)));
-            w[q] = e;
+            // |E|^2 after the (unit-modulus) screen is |E|^2 before it, to the
+            // phasor's rounding; taken first it does not wait for the phasor
+            const float2 wq = w[q];
             if (irow) {
-              const float iv = fmaf(e.x, e.x, e.y * e.y);
+              const float iv = fmaf(wq.x, wq.x, wq.y * wq.y);
               if (i_smem) irow[x] = iv;
               else __stcs(irow + x, iv);
             }
+            w[q] = cmul(wq, phasor(fmaf(a.screen_c, dval[q], c0)));
           }
         };
         if constexpr (KAPPA) {
