@@ -95,6 +95,18 @@ int bpm_corrector_apply(bpm_corrector_t c, void *d_field, const void *d_dn, floa
  * factor + k], k < factor), zc < nz / factor; volumes [z][ny][nx] FP16. */
 int bpm_coarsen_index(const void *d_dn, int nz, int ny, int nx, int factor, void *d_out, cudaStream_t stream);
 
+/* Inference engine of bpm_corrector_forward and bpm_corrector_apply: on != 0
+ * (the default) runs the four convolutions on the tensor cores (tcgen05
+ * kind::f16: BF16 activations and weights in shared memory, FP32 accumulators
+ * in tensor memory, one 128-pixel row segment per MMA tile) whenever w is a
+ * multiple of 128, else on the FP32 pipes; on = 0 always uses the FP32 pipes
+ * (FP32 activations), as training does. */
+int bpm_corrector_set_tensor_cores(bpm_corrector_t c, int on);
+
+/* Synchronise the stream and report a device error of the tensor-core path
+ * (BPM_ERR_TIMEOUT when a bounded wait gave up). */
+int bpm_corrector_check(bpm_corrector_t c, cudaStream_t stream);
+
 int bpm_corrector_free(bpm_corrector_t c);
 const char *bpm_corrector_last_error(void);
 

@@ -102,14 +102,27 @@ def conv_weight_grad(X: np.ndarray, dY: np.ndarray):
     return dW, dY.sum(axis=(0, 2, 3))
 
 
-def forward(theta: np.ndarray, X: np.ndarray, sigma: float = 1.0):
-    """Network output and the intermediate tensors backpropagation needs."""
+def round_bf16(a: np.ndarray) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even) after rounding to float32:
+    keep the upper 16 bits of the float32 pattern, adding half of the dropped
+    part plus the kept part's lowest bit (round half to even)."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(theta: np.ndarray, X: np.ndarray, sigma: float = 1.0, act_bf16: bool = False):
+    """Network output and the intermediate tensors backpropagation needs.
+    With ``act_bf16`` every convolution's input (the packed field and the
+    three hidden activations) is rounded to bfloat16 first, the arithmetic
+    of an inference engine that keeps activations in bfloat16 and
+    accumulates exactly (here in float64)."""
     c_in = X.shape[1]
     layers = unflatten(theta, c_in)
     acts, pre = [X], []
     A = X
     for k, (W, b) in enumerate(layers):
-        Z = conv(A, W, b)
+        Z = conv(round_bf16(A) if act_bf16 else A, W, b)
         pre.append(Z)
         A = np.maximum(Z, 0.0) if k < LAYERS - 1 else Z
         acts.append(A)

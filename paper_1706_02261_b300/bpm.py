@@ -296,6 +296,8 @@ _lib.bpm_corrector_pack.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_float, _vp, _vp
 _lib.bpm_corrector_apply.argtypes = [_vp, _vp, _vp, ctypes.c_float, _i, _i, _vp]
 _lib.bpm_coarsen_index.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp]
 _lib.bpm_corrector_free.argtypes = [_vp]
+_lib.bpm_corrector_set_tensor_cores.argtypes = [_vp, _i]
+_lib.bpm_corrector_check.argtypes = [_vp, _vp]
 _lib.bpm_corrector_last_error.restype = ctypes.c_char_p
 for _f in ("bpm_corrector_create", "bpm_corrector_param_count", "bpm_corrector_set_params",
            "bpm_corrector_get_params", "bpm_corrector_forward", "bpm_corrector_loss_grad", "bpm_corrector_adam",
@@ -363,6 +365,13 @@ class Corrector:
     def apply(self, field, dn=None, dn_scale: float = 0.0, stream=None):
         hh, ww = field.shape
         _ccheck(_lib.bpm_corrector_apply(self.h, _ptr(field), _ptr(dn), dn_scale, hh, ww, _stream_handle(stream)))
+
+    def set_tensor_cores(self, on: bool):
+        """Inference on the tensor cores (BF16 activations) or on the FP32 pipes."""
+        _ccheck(_lib.bpm_corrector_set_tensor_cores(self.h, int(bool(on))))
+
+    def check(self, stream=None):
+        _ccheck(_lib.bpm_corrector_check(self.h, _stream_handle(stream)))
 
     def free(self):
         if self.h:

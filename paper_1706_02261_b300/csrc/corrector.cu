@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include <algorithm>
 #include <cmath>
@@ -263,20 +264,35 @@ __global__ void corr_round_bf16(const float* __restrict__ master, float* __restr
 
 // Per-field RMS amplitude a[b] = sqrt(mean |E|^2) (FP64 accumulation), one
 // CTA per field; a field of zeros gets a = 1.
-__global__ void corr_field_rms(const float2* __restrict__ field, int hw, float* __restrict__ amp) {
-  __shared__ double red[256];
-  const float2* f = field + (size_t)blockIdx.x * hw;
-  double s = 0.0;
-  for (int p = threadIdx.x; p < hw; p += 256) s += (double)f[p].x * f[p].x + (double)f[p].y * f[p].y;
+// RMS amplitude of each field (the normalisation the network sees; pack and
+// unpack use the same value, so it needs no more than FP32 partial sums):
+// kRmsChunks blocks per field sum |E|^2 over their share, then one warp per
+// field combines the partials in a fixed order.
+constexpr int kRmsChunks = 64;
+__global__ void corr_field_rms_partial(const float2* __restrict__ field, int hw, float* __restrict__ partial) {
+  __shared__ float red[256];
+  const float2* f = field + (size_t)blockIdx.y * hw;
+  const int per = (hw + kRmsChunks - 1) / kRmsChunks;
+  const int p0 = blockIdx.x * per, p1 = min(hw, p0 + per);
+  float s = 0.f;
+  for (int p = p0 + threadIdx.x; p < p1; p += 256) s = fmaf(f[p].x, f[p].x, fmaf(f[p].y, f[p].y, s));
   red[threadIdx.x] = s;
   __syncthreads();
   for (int k = 128; k > 0; k >>= 1) {
     if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
     __syncthreads();
   }
+  if (threadIdx.x == 0) partial[blockIdx.y * kRmsChunks + blockIdx.x] = red[0];
+}
+__global__ void corr_field_rms_final(const float* __restrict__ partial, int hw, float* __restrict__ amp) {
+  // one warp: lane l adds partials l, l + 32, ...; then a fixed shuffle tree
+  float t = 0.f;
+  for (int k = threadIdx.x; k < kRmsChunks; k += 32) t += partial[blockIdx.x * kRmsChunks + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
   if (threadIdx.x == 0) {
-    const double a = sqrt(red[0] / hw);
-    amp[blockIdx.x] = a > 0.0 ? (float)a : 1.0f;
+    const float a = sqrtf(t / (float)hw);
+    amp[blockIdx.x] = a > 0.f ? a : 1.0f;
   }
 }
 
@@ -325,6 +341,374 @@ __global__ void coarsen_index(const __half* __restrict__ dn, int nzc, size_t pla
 
 int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 148 * 16); }
 
+// ---------------------------------------------------------------------------
+// Tensor-core inference path (tcgen05): each convolution as an implicit GEMM
+// D[pixel][c_out] = sum over taps and c_in of A[pixel + tap][c_in] W[tap][c_in][c_out],
+// BF16 operands in shared memory, FP32 accumulators in tensor memory.
+//
+// Activations of this path are BF16 in channel chunks of 8 with the circular
+// halo stored in every row: [b][c / 8][y][W + 2][8], pixel x at column x + 1,
+// column 0 repeating pixel W - 1 and column W + 1 pixel 0 (16 bytes per pixel
+// and chunk), so a tile's input row with its halo is one contiguous copy, and
+// the operand of a tap shifted by one pixel starts 16 bytes further: a K-major,
+// unswizzled operand (core matrices of 8 pixels x 8 channels, 16 bytes per
+// row) whose next 8 channels sit one chunk further (the leading byte offset)
+// and whose next 8 pixels sit 128 bytes further (the stride byte offset).
+// Weights: [tap][c_in / 8][c_out][8].
+// ---------------------------------------------------------------------------
+namespace tc {
+
+constexpr int kM = 128;                 // output pixels per tile (one row segment)
+constexpr int kPix = kM + 2;            // with the two halo pixels
+constexpr int kThreadsTc = 128;         // four warps: one per quarter of the tensor-memory lanes
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// shared-memory operand descriptor: start, leading (K) and stride (M/N) byte
+// offsets in 16-byte units, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t operand_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* m) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(m)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase with this parity; records a timeout in err.  The
+// global timer is read only when the phase is not complete at once, and then
+// every 64 polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, int* err) {
+  if (mbar_try(m, parity)) return true;
+  const unsigned long long t0 = gtime();
+  for (unsigned n = 1;; ++n) {
+    if (mbar_try(m, parity)) return true;
+    if ((n & 63) == 0 && gtime() - t0 > kWaitNs) {
+      atomicCAS(err, 0, BPM_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(m))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, int accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t* m) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(m))
+               : "memory");
+}
+// 32 consecutive accumulator columns of this warp's 32 lanes (one pixel per thread)
+__device__ __forceinline__ void ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+enum ConvOut { OUT_HIDDEN = 0, OUT_PLANES = 1, OUT_FIELD = 2 };
+
+constexpr int kRowsTc = 2;              // output rows per tile
+
+__host__ __device__ constexpr int tmem_cols(int n) { return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : 256)); }
+
+// One 3x3 circular convolution layer.  CIN, COUT: channel counts padded to
+// multiples of 16.  A tile is kRowsTc output rows x 128 pixels; its kRowsTc + 2
+// input rows (with the two circular halo pixels) are fetched by bulk copies
+// into one of two shared-memory buffers while the previous tile is computed,
+// each output row's accumulators take COUT tensor-memory columns, and the
+// four warps read them back (warp w: pixels 32w..32w+31).  Outputs:
+//   OUT_HIDDEN  bias + ReLU, BF16 chunks [b][COUT/8][y][x][8]
+//   OUT_PLANES  bias, the first cout_real channels as FP32 planes [b][c][y][x]
+//   OUT_FIELD   bias, then field[b][y][x] += sigma amp[b] (f0, f1): the
+//               residual update of the un-normalised field (apply)
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(kThreadsTc) conv_tc(const __nv_bfloat16* __restrict__ in,
+                                                      const __nv_bfloat16* __restrict__ wtc,
+                                                      const float* __restrict__ bias, int cout_real,
+                                                      __nv_bfloat16* __restrict__ out_bf, float* __restrict__ out_f,
+                                                      float2* __restrict__ field, const float* __restrict__ amp,
+                                                      float sigma, int B, int H, int W, int* err) {
+  static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 32, "padded channel counts");
+  constexpr int R = kRowsTc;
+  constexpr int KC = CIN / 8;
+  constexpr int ROWB = KC * kPix * 16;            // one input row (all chunks) in shared memory
+  constexpr int TILEB = (R + 2) * ROWB;
+  constexpr int WBYTES = 9 * KC * COUT * 16;
+  constexpr int NCOL = tmem_cols(R * COUT);
+  extern __shared__ __align__(128) unsigned char sm[];
+  unsigned char* sW = sm;
+  unsigned char* const sA0 = sm + ((WBYTES + 127) & ~127);
+  auto sA = [&](int buf) { return sA0 + (buf ? TILEB : 0); };
+  __shared__ __align__(8) uint64_t bar_load[2], bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ float s_bias[32];
+  const int tiles_x = W / kM, tiles_y = H / R, tiles = B * tiles_y * tiles_x;
+  // rows y0-1 .. y0+R (circular), pixels x0-1 .. x0+128 (the stored halo), every chunk
+  auto issue_load = [&](int tile, int buf) {
+    const int tx = tile % tiles_x, y0 = ((tile / tiles_x) % tiles_y) * R, b = tile / (tiles_x * tiles_y);
+    const int x0 = tx * kM;
+    mbar_expect_tx(&bar_load[buf], (R + 2) * KC * kPix * 16);
+    for (int r = 0; r < R + 2; ++r) {
+      const int yy = (y0 + r - 1 + H) % H;
+      for (int c = 0; c < KC; ++c) {
+        // columns x0 .. x0 + 129 of the padded row: pixels x0 - 1 .. x0 + 128
+        const __nv_bfloat16* row = in + (((size_t)b * KC + c) * H + yy) * (size_t)(W + 2) * 8;
+        bulk_g2s(sA(buf) + r * ROWB + c * kPix * 16, row + (size_t)x0 * 8, kPix * 16, &bar_load[buf]);
+      }
+    }
+  };
+  // the first tile's rows are on their way while the weights are copied
+  if (threadIdx.x == 0) {
+    mbar_init(&bar_load[0]);
+    mbar_init(&bar_load[1]);
+    mbar_init(&bar_mma);
+    if ((int)blockIdx.x < tiles) issue_load(blockIdx.x, 0);
+  }
+  for (int i = threadIdx.x; i < WBYTES / 16; i += kThreadsTc)
+    reinterpret_cast<uint4*>(sW)[i] = __ldg(reinterpret_cast<const uint4*>(wtc) + i);
+  if (threadIdx.x < 32) s_bias[threadIdx.x] = threadIdx.x < cout_real ? bias[threadIdx.x] : 0.f;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // weights: generic writes -> tensor-core reads
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                 "r"(NCOL)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base;
+  uint32_t ph_load = 0u, ph_mma = 0u;      // parity of each load buffer (bit buf)
+  uint32_t pending = (int)blockIdx.x < tiles ? 1u : 0u;   // load buffers with a copy in flight (bit buf)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int it = 0;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+    const int buf = it & 1;
+    const int tx = tile % tiles_x, y0 = ((tile / tiles_x) % tiles_y) * R, b = tile / (tiles_x * tiles_y);
+    const int x0 = tx * kM;
+    bool ok = mbar_wait(&bar_load[buf], (ph_load >> buf) & 1u, err);
+    ph_load ^= 1u << buf;
+    pending &= ~(1u << buf);
+    if (__syncthreads_or(!ok)) break;
+    const int next = tile + gridDim.x;
+    if (threadIdx.x == 0) {
+      fence_after();
+      constexpr uint32_t idesc = instr_desc(kM, COUT);
+      // descriptors built once per tile; an operand further into shared
+      // memory only adds its offset in 16-byte units to the start field
+      // (shared addresses stay below 2^18 bytes, so the 14-bit field never carries)
+      const uint64_t a0 = operand_desc(saddr(sA(buf)), kPix * 16, 128);
+      const uint64_t b0 = operand_desc(saddr(sW), COUT * 16, 128);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+          for (int kk = 0; kk < KC / 2; ++kk) {
+            const uint32_t a_off = (r + dy) * ROWB + (2 * kk) * kPix * 16 + dx * 16;
+            const uint32_t b_off = (tap * KC + 2 * kk) * COUT * 16;
+            mma(tmem + r * COUT, a0 + (a_off >> 4), b0 + (b_off >> 4), idesc, tap > 0 || kk > 0);
+          }
+        }
+      }
+      commit(&bar_mma);
+      // the other buffer was last read by the previous tile's MMAs, which have completed
+      if (next < tiles) issue_load(next, buf ^ 1);
+    }
+    if (next < tiles) pending |= 1u << (buf ^ 1);
+    ok = mbar_wait(&bar_mma, ph_mma, err);
+    ph_mma ^= 1u;
+    fence_after();
+    if (ok) {
+      const int m = 32 * warp + lane;
+      const uint32_t lanes = (uint32_t)(32 * warp) << 16;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int y = y0 + r;
+        if constexpr (MODE == OUT_HIDDEN) {
+          float v[32];
+          ld32(tmem + lanes + r * COUT, v);
+#pragma unroll
+          for (int j = 0; j < COUT / 8; ++j) {
+            uint32_t packed[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float lo = fmaxf(v[8 * j + 2 * e] + s_bias[8 * j + 2 * e], 0.f);
+              const float hi = fmaxf(v[8 * j + 2 * e + 1] + s_bias[8 * j + 2 * e + 1], 0.f);
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
+              packed[e] = *reinterpret_cast<const uint32_t*>(&h2);
+            }
+            const uint4 q = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            uint4* row = reinterpret_cast<uint4*>(out_bf + (((size_t)b * (COUT / 8) + j) * H + y) * (size_t)(W + 2) * 8);
+            const int x = x0 + m;
+            row[x + 1] = q;
+            if (x == W - 1) row[0] = q;            // the halo copies of the row ends
+            if (x == 0) row[W + 1] = q;
+          }
+        } else {
+          float v[16];
+          ld16(tmem + lanes + r * COUT, v);
+          const float f0 = v[0] + s_bias[0], f1 = v[1] + s_bias[1];
+          if constexpr (MODE == OUT_PLANES) {
+            out_f[(((size_t)b * cout_real + 0) * H + y) * W + x0 + m] = f0;
+            if (cout_real > 1) out_f[(((size_t)b * cout_real + 1) * H + y) * W + x0 + m] = f1;
+          } else {
+            const float s = sigma * amp[b];
+            float2* e = field + ((size_t)b * H + y) * W + x0 + m;
+            const float2 old = *e;
+            *e = make_float2(fmaf(s, f0, old.x), fmaf(s, f1, old.y));
+          }
+        }
+      }
+    }
+    fence_before();
+    if (__syncthreads_or(!ok)) break;     // accumulators are free for the next tile
+  }
+  // leave no bulk copy in flight (only after a failed wait can one remain)
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 2; ++k)
+      if ((pending >> k) & 1u) mbar_wait(&bar_load[k], (ph_load >> k) & 1u, err);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL) : "memory");
+}
+
+template <int CIN, int COUT>
+constexpr size_t conv_tc_smem() {
+  return ((size_t)(9 * (CIN / 8) * COUT * 16 + 127) & ~(size_t)127) + 2 * (size_t)(kRowsTc + 2) * (CIN / 8) * kPix * 16;
+}
+
+// store the two 16-byte chunks of one pixel into the padded chunk layout
+// [b][2][y][W + 2][8], with the halo copies at the row ends
+__device__ __forceinline__ void store_pixel_chunks(__nv_bfloat16* out, size_t b, int y, int x, int H, int W,
+                                                   uint4 c0, uint4 c1) {
+  uint4* r0 = reinterpret_cast<uint4*>(out + (((b * 2 + 0) * H + y) * (size_t)(W + 2)) * 8);
+  uint4* r1 = reinterpret_cast<uint4*>(out + (((b * 2 + 1) * H + y) * (size_t)(W + 2)) * 8);
+  r0[x + 1] = c0;
+  r1[x + 1] = c1;
+  if (x == W - 1) {
+    r0[0] = c0;
+    r1[0] = c1;
+  }
+  if (x == 0) {
+    r0[W + 1] = c0;
+    r1[W + 1] = c1;
+  }
+}
+
+// packed FP32 input [b][cin][y][x] -> BF16 chunks (padded layout; channels >= cin zero)
+__global__ void to_chunks(const float* __restrict__ x, int cin, int B, int H, int W, __nv_bfloat16* __restrict__ out) {
+  const int hw = H * W;
+  const size_t n = (size_t)B * hw;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / hw, p = i % hw;
+    float c[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) c[k] = k < cin ? x[(b * cin + k) * hw + p] : 0.f;
+    uint4 q[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      uint32_t packed[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(c[8 * j + 2 * e], c[8 * j + 2 * e + 1]);
+        packed[e] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+      q[j] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    }
+    store_pixel_chunks(out, b, (int)(p / W), (int)(p % W), H, W, q[0], q[1]);
+  }
+}
+
+// apply: the field normalised by its RMS amplitude (and the index channel)
+// straight into BF16 chunks [b][2][y][x][8]
+__global__ void field_to_chunks(const float2* __restrict__ field, const __half* __restrict__ dn, float dn_scale,
+                                const float* __restrict__ amp, int cin, int B, int H, int W,
+                                __nv_bfloat16* __restrict__ out) {
+  const int hw = H * W;
+  const size_t n = (size_t)B * hw;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / hw, p = i % hw;
+    const float inv = 1.0f / amp[b];
+    const float2 e = field[i];
+    const float c2 = (cin > 2 && dn) ? dn_scale * __half2float(dn[i]) : 0.f;
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(e.x * inv, e.y * inv);
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(cin > 2 ? c2 : 0.f, 0.f);
+    const uint32_t w0 = *reinterpret_cast<const uint32_t*>(&h0), w1 = *reinterpret_cast<const uint32_t*>(&h1);
+    store_pixel_chunks(out, b, (int)(p / W), (int)(p % W), H, W, make_uint4(w0, w1, 0u, 0u), make_uint4(0u, 0u, 0u, 0u));
+  }
+}
+
+// layer weights W[o][c][3][3] (FP32 values already rounded to BF16) -> [tap][c/8][o][8] BF16, zero padded
+__global__ void pack_weights(const float* __restrict__ Wl, int cin, int cout, int cinp, int coutp,
+                             __nv_bfloat16* __restrict__ out) {
+  const int n = 9 * cinp * coutp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int e = i % 8, o = (i / 8) % coutp, kc = (i / (8 * coutp)) % (cinp / 8), tap = i / (8 * coutp * (cinp / 8));
+    const int c = kc * 8 + e;
+    const float w = (o < cout && c < cin) ? Wl[((size_t)o * cin + c) * 9 + tap] : 0.f;
+    out[i] = __float2bfloat16_rn(w);
+  }
+}
+
+}  // namespace tc
+
 }  // namespace
 
 struct bpm_corrector_s {
@@ -336,15 +720,25 @@ struct bpm_corrector_s {
   float *z[4] = {}, *a[3] = {};    // pre-activations and activations
   float *d0 = nullptr, *d1 = nullptr;   // backpropagated gradients (ping-pong)
   float *partial = nullptr, *lpart = nullptr, *loss = nullptr, *outbuf = nullptr, *amp = nullptr;
+  float* rms_part = nullptr;       // per-field partial sums of |E|^2
   size_t partial_floats = 0;
   int step = 0;
   float sigma = 1.0f;              // residual scale: out = x[:, :2] + sigma f(x)
+  // tensor-core inference path
+  int use_tc = 1;                  // inference on tcgen05 when the width is a multiple of 128
+  __nv_bfloat16* xtc = nullptr;    // input as BF16 chunks [B][2][H][W][8]
+  __nv_bfloat16* atc[2] = {};      // hidden activations as BF16 chunks [B][4][H][W][8]
+  __nv_bfloat16* wtc[4] = {};      // layer weights [tap][c_in/8][c_out][8]
+  int* err = nullptr;              // device error word (bounded waits)
+  unsigned wver = 1, tcver = 0;    // versions of the working weights and of their packed copy
 };
 
 namespace {
 
 int layer_in(const bpm_corrector_s* c, int l) { return l == 0 ? c->cin : kCh; }
 int layer_out(int l) { return l == 3 ? 2 : kCh; }
+int layer_in_padded(int l) { return l == 0 ? 16 : kCh; }
+int layer_out_padded(int l) { return l == 3 ? 16 : kCh; }
 
 template <class K>
 int set_smem(K kernel, size_t bytes) {
@@ -366,6 +760,10 @@ int setup_attrs() {
   rc |= set_smem(corr_wgrad<3, kCh>, wgrad_smem<3, kCh>());
   rc |= set_smem(corr_wgrad<kCh, kCh>, wgrad_smem<kCh, kCh>());
   rc |= set_smem(corr_wgrad<kCh, 2>, wgrad_smem<kCh, 2>());
+  rc |= set_smem(tc::conv_tc<16, kCh, tc::OUT_HIDDEN>, tc::conv_tc_smem<16, kCh>());
+  rc |= set_smem(tc::conv_tc<kCh, kCh, tc::OUT_HIDDEN>, tc::conv_tc_smem<kCh, kCh>());
+  rc |= set_smem(tc::conv_tc<kCh, 16, tc::OUT_PLANES>, tc::conv_tc_smem<kCh, 16>());
+  rc |= set_smem(tc::conv_tc<kCh, 16, tc::OUT_FIELD>, tc::conv_tc_smem<kCh, 16>());
   if (rc) return BPM_ERR_CUDA;
   done = true;
   return BPM_OK;
@@ -395,6 +793,71 @@ int forward(bpm_corrector_s* c, const float* x, int batch, int h, int w, cudaStr
       c->a[2], c->work + c->off[6], c->work + c->off[7], nullptr, c->z[3], nullptr, h, w);
   CORR_CU(cudaGetLastError());
   return BPM_OK;
+}
+
+// BF16 copy of the working weights in the tensor-core layout, refreshed when
+// the working weights have changed
+void ensure_tc_weights(bpm_corrector_s* c, cudaStream_t s) {
+  if (c->tcver == c->wver) return;
+  for (int l = 0; l < 4; ++l) {
+    const int n = 9 * layer_in_padded(l) * layer_out_padded(l);
+    tc::pack_weights<<<(n + 255) / 256, 256, 0, s>>>(c->work + c->off[2 * l], layer_in(c, l), layer_out(l),
+                                                      layer_in_padded(l), layer_out_padded(l), c->wtc[l]);
+  }
+  c->tcver = c->wver;
+}
+
+// the three hidden layers on the tensor cores: xtc -> atc[0] -> atc[1] -> atc[0]
+int hidden_tc(bpm_corrector_s* c, int batch, int h, int w, int grid, cudaStream_t s) {
+  tc::conv_tc<16, kCh, tc::OUT_HIDDEN><<<grid, tc::kThreadsTc, tc::conv_tc_smem<16, kCh>(), s>>>(
+      c->xtc, c->wtc[0], c->work + c->off[1], kCh, c->atc[0], nullptr, nullptr, nullptr, 0.f, batch, h, w, c->err);
+  tc::conv_tc<kCh, kCh, tc::OUT_HIDDEN><<<grid, tc::kThreadsTc, tc::conv_tc_smem<kCh, kCh>(), s>>>(
+      c->atc[0], c->wtc[1], c->work + c->off[3], kCh, c->atc[1], nullptr, nullptr, nullptr, 0.f, batch, h, w, c->err);
+  tc::conv_tc<kCh, kCh, tc::OUT_HIDDEN><<<grid, tc::kThreadsTc, tc::conv_tc_smem<kCh, kCh>(), s>>>(
+      c->atc[1], c->wtc[2], c->work + c->off[5], kCh, c->atc[0], nullptr, nullptr, nullptr, 0.f, batch, h, w, c->err);
+  CORR_CU(cudaGetLastError());
+  return BPM_OK;
+}
+
+int tc_grid(int batch, int h, int w) {
+  const int tiles = batch * (h / tc::kRowsTc) * (w / tc::kM);
+  return std::max(1, std::min(tiles, 148 * 2));
+}
+
+// forward pass on the tensor cores (inference): z[3] = f(x) before the
+// residual, from the packed FP32 input; activations BF16, accumulation FP32
+int forward_tc(bpm_corrector_s* c, const float* x, int batch, int h, int w, cudaStream_t s) {
+  ensure_tc_weights(c, s);
+  const int hw = h * w;
+  tc::to_chunks<<<grid_for((size_t)batch * hw), 256, 0, s>>>(x, c->cin, batch, h, w, c->xtc);
+  const int grid = tc_grid(batch, h, w);
+  int rc = hidden_tc(c, batch, h, w, grid, s);
+  if (rc) return rc;
+  tc::conv_tc<kCh, 16, tc::OUT_PLANES><<<grid, tc::kThreadsTc, tc::conv_tc_smem<kCh, 16>(), s>>>(
+      c->atc[0], c->wtc[3], c->work + c->off[7], 2, nullptr, c->z[3], nullptr, nullptr, 0.f, batch, h, w, c->err);
+  CORR_CU(cudaGetLastError());
+  return BPM_OK;
+}
+
+// apply on the tensor cores: normalised field (and index) straight into BF16
+// chunks, the network, and the residual update of the field in place
+int apply_tc(bpm_corrector_s* c, float2* field, const __half* dn, float dn_scale, int h, int w, cudaStream_t s) {
+  ensure_tc_weights(c, s);
+  const int hw = h * w;
+  tc::field_to_chunks<<<grid_for((size_t)hw), 256, 0, s>>>(field, dn, dn_scale, c->amp, c->cin, 1, h, w, c->xtc);
+  const int grid = tc_grid(1, h, w);
+  int rc = hidden_tc(c, 1, h, w, grid, s);
+  if (rc) return rc;
+  tc::conv_tc<kCh, 16, tc::OUT_FIELD><<<grid, tc::kThreadsTc, tc::conv_tc_smem<kCh, 16>(), s>>>(
+      c->atc[0], c->wtc[3], c->work + c->off[7], 2, nullptr, nullptr, field, c->amp, c->sigma, 1, h, w, c->err);
+  CORR_CU(cudaGetLastError());
+  return BPM_OK;
+}
+
+// inference forward: the tensor-core path when enabled and the width allows it
+int forward_infer(bpm_corrector_s* c, const float* x, int batch, int h, int w, cudaStream_t s) {
+  if (c->use_tc && w % tc::kM == 0) return forward_tc(c, x, batch, h, w, s);
+  return forward(c, x, batch, h, w, s);
 }
 
 // loss and full gradient (into c->grad) for packed x and target [B][2][H][W]
@@ -480,6 +943,20 @@ extern "C" int bpm_corrector_create(bpm_corrector_t* out, int in_channels, int m
   alloc(&c->loss, 1);
   alloc(&c->outbuf, (size_t)max_batch * 2 * max_h * max_w);
   alloc(&c->amp, (size_t)max_batch);
+  alloc(&c->rms_part, (size_t)max_batch * kRmsChunks);
+  auto alloc_bf = [&](__nv_bfloat16** p, size_t n) {
+    if (ok && cudaMalloc(p, n * sizeof(__nv_bfloat16)) != cudaSuccess) ok = false;
+  };
+  // padded rows (W + 2 pixels) for the tensor-core layout: h (w + 2) = h w + 2h
+  // with h w <= max_h max_w and w >= 16, so at most 9/8 of max_h max_w
+  const size_t pad_hw = (size_t)max_h * max_w + 2 * ((size_t)max_h * max_w / 16);
+  const size_t act_pad = (size_t)max_batch * kCh * pad_hw;
+  alloc_bf(&c->xtc, (size_t)max_batch * 16 * pad_hw);
+  alloc_bf(&c->atc[0], act_pad);
+  alloc_bf(&c->atc[1], act_pad);
+  for (int l = 0; l < 4; ++l) alloc_bf(&c->wtc[l], (size_t)9 * layer_in_padded(l) * layer_out_padded(l));
+  if (ok && cudaMalloc(&c->err, sizeof(int)) != cudaSuccess) ok = false;
+  if (ok) cudaMemsetAsync(c->err, 0, sizeof(int), stream);
   if (!ok) {
     cudaGetLastError();
     bpm_corrector_free(c);
@@ -514,6 +991,7 @@ extern "C" int bpm_corrector_set_params(bpm_corrector_t c, const float* h_params
   CORR_CU(cudaGetLastError());
   CORR_CU(cudaStreamSynchronize(stream));
   c->step = 0;
+  ++c->wver;
   return BPM_OK;
 }
 
@@ -530,7 +1008,7 @@ extern "C" int bpm_corrector_forward(bpm_corrector_t c, const float* d_x, float*
   if (!c || !d_x || !d_out) return cfail(BPM_ERR_ARG, "NULL argument");
   int rc = check_dims(c, batch, h, w);
   if (rc) return rc;
-  rc = forward(c, d_x, batch, h, w, stream);
+  rc = forward_infer(c, d_x, batch, h, w, stream);
   if (rc) return rc;
   corr_residual<<<grid_for((size_t)batch * 2 * h * w), 256, 0, stream>>>(d_x, c->cin, c->z[3], c->sigma, d_out,
                                                                          batch, h * w);
@@ -560,6 +1038,7 @@ extern "C" int bpm_corrector_adam(bpm_corrector_t c, float lr, cudaStream_t stre
   corr_adam<<<(c->P + 255) / 256, 256, 0, stream>>>(c->master, c->work, c->m, c->v, c->grad, c->P, lr, (float)b1,
                                                     (float)b2, c1, c2, 1e-8f);
   CORR_CU(cudaGetLastError());
+  ++c->wver;
   return BPM_OK;
 }
 
@@ -575,7 +1054,9 @@ extern "C" int bpm_corrector_pack(bpm_corrector_t c, const void* d_fields, const
                                   cudaStream_t stream) {
   if (!c || !d_fields || !d_x || (d_targets && !d_t)) return cfail(BPM_ERR_ARG, "NULL argument");
   if (batch < 1 || batch > c->maxb || h < 1 || w < 1) return cfail(BPM_ERR_ARG, "bad sizes (batch <= %d)", c->maxb);
-  corr_field_rms<<<batch, 256, 0, stream>>>(static_cast<const float2*>(d_fields), h * w, c->amp);
+  corr_field_rms_partial<<<dim3(kRmsChunks, batch), 256, 0, stream>>>(static_cast<const float2*>(d_fields), h * w,
+                                                                     c->rms_part);
+  corr_field_rms_final<<<batch, 32, 0, stream>>>(c->rms_part, h * w, c->amp);
   corr_pack<<<grid_for((size_t)batch * h * w), 256, 0, stream>>>(
       static_cast<const float2*>(d_fields), static_cast<const float2*>(d_targets), static_cast<const __half*>(d_dn),
       dn_scale, c->amp, d_x, d_t, c->cin, batch, h * w);
@@ -588,11 +1069,15 @@ extern "C" int bpm_corrector_apply(bpm_corrector_t c, void* d_field, const void*
   if (!c || !d_field) return cfail(BPM_ERR_ARG, "NULL argument");
   int rc = check_dims(c, 1, h, w);
   if (rc) return rc;
-  corr_field_rms<<<1, 256, 0, stream>>>(static_cast<const float2*>(d_field), h * w, c->amp);
+  corr_field_rms_partial<<<dim3(kRmsChunks, 1), 256, 0, stream>>>(static_cast<const float2*>(d_field), h * w,
+                                                                 c->rms_part);
+  corr_field_rms_final<<<1, 32, 0, stream>>>(c->rms_part, h * w, c->amp);
+  if (c->use_tc && w % tc::kM == 0)
+    return apply_tc(c, static_cast<float2*>(d_field), static_cast<const __half*>(d_dn), dn_scale, h, w, stream);
   corr_pack<<<grid_for((size_t)h * w), 256, 0, stream>>>(static_cast<const float2*>(d_field), nullptr,
                                                           static_cast<const __half*>(d_dn), dn_scale, c->amp, c->x,
                                                           nullptr, c->cin, 1, h * w);
-  rc = forward(c, c->x, 1, h, w, stream);
+  rc = forward_infer(c, c->x, 1, h, w, stream);
   if (rc) return rc;
   corr_residual<<<grid_for((size_t)2 * h * w), 256, 0, stream>>>(c->x, c->cin, c->z[3], c->sigma, c->outbuf, 1,
                                                                   h * w);
@@ -614,11 +1099,32 @@ extern "C" int bpm_coarsen_index(const void* d_dn, int nz, int ny, int nx, int f
   return BPM_OK;
 }
 
+extern "C" int bpm_corrector_set_tensor_cores(bpm_corrector_t c, int on) {
+  if (!c) return cfail(BPM_ERR_ARG, "corrector is NULL");
+  c->use_tc = on ? 1 : 0;
+  return BPM_OK;
+}
+
+extern "C" int bpm_corrector_check(bpm_corrector_t c, cudaStream_t stream) {
+  if (!c) return cfail(BPM_ERR_ARG, "corrector is NULL");
+  CORR_CU(cudaStreamSynchronize(stream));
+  int e = 0;
+  CORR_CU(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) return cfail(e, "a tensor-core convolution gave up waiting for its data or its MMAs");
+  return BPM_OK;
+}
+
 extern "C" int bpm_corrector_free(bpm_corrector_t c) {
   if (!c) return BPM_OK;
   float* bufs[] = {c->master, c->work, c->m, c->v, c->grad, c->x, c->z[0], c->z[1], c->z[2], c->z[3],
                    c->a[0], c->a[1], c->a[2], c->d0, c->d1, c->partial, c->lpart, c->loss, c->outbuf, c->amp};
   for (float* b : bufs) cudaFree(b);
+  cudaFree(c->xtc);
+  cudaFree(c->atc[0]);
+  cudaFree(c->atc[1]);
+  for (int l = 0; l < 4; ++l) cudaFree(c->wtc[l]);
+  cudaFree(c->err);
+  cudaFree(c->rms_part);
   delete c;
   return BPM_OK;
 }

@@ -118,3 +118,65 @@ def test_training_gains_over_coarse_steps_on_held_out_seeds(B, c_in, min_gain):
         assert gain > min_gain, ev
     finally:
         corr.free()
+
+
+@pytest.mark.parametrize("c_in,h,w", [(2, 32, 128), (3, 16, 256)])
+def test_tensor_core_forward_matches_bf16_activation_oracle(B, c_in, h, w):
+    """The tcgen05 inference engine (BF16 activations and weights, FP32
+    accumulation in tensor memory) against the oracle with the same BF16
+    rounding of every convolution input; tiles of 128 pixels, circular
+    halos across the row ends and the image edges."""
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(20 + c_in)
+    theta = inputs.corrector_init(c_in, 5) + 0.05 * rng.standard_normal(inputs.corrector_param_count(c_in))
+    bsz = 2
+    X = rng.standard_normal((bsz, c_in, h, w)).astype(np.float32)
+    corr = B.Corrector(c_in, 4, 32, 256)
+    sigma = 0.37
+    try:
+        corr.set_residual_scale(sigma)
+        corr.set_params(theta.astype(np.float32))
+        work = corr.get_params(which=1).astype(np.float64)
+        xd = torch.from_numpy(X).to(dev)
+        out = torch.empty((bsz, 2, h, w), dtype=torch.float32, device=dev)
+        corr.set_tensor_cores(True)
+        corr.forward(xd, out)
+        corr.check()
+        f_gpu = (out.cpu().numpy().astype(np.float64) - X[:, :2]) / sigma
+        ref, _, _ = oc.forward(work, X.astype(np.float64), sigma, act_bf16=True)
+        f_ref = (ref - X[:, :2]) / sigma
+        e = rel(f_gpu, f_ref)
+        corr.set_tensor_cores(False)
+        corr.forward(xd, out)
+        f_fp32 = (out.cpu().numpy().astype(np.float64) - X[:, :2]) / sigma
+        print(f"c_in={c_in} {h}x{w}: tensor cores vs BF16-activation oracle {e:.2e}; "
+              f"FP32 pipes vs the same {rel(f_fp32, f_ref):.2e}")
+        assert e <= 5e-4
+    finally:
+        corr.free()
+
+
+def test_apply_on_tensor_cores_agrees_with_fp32_pipes_at_512(B):
+    from paper_1706_02261_b300 import corrector as C
+    dev = torch.device("cuda")
+    s = C.Setup(n=512, nz=8, c_in=3)
+    corr = B.Corrector(3, 1, 512, 512)
+    try:
+        rng = np.random.default_rng(2)
+        corr.set_params((inputs.corrector_init(3, 0) + 0.02 * rng.standard_normal(inputs.corrector_param_count(3)))
+                        .astype(np.float32))
+        corr.set_residual_scale(0.05)
+        dnc = torch.from_numpy(rng.uniform(0, 0.05, (512, 512)).astype(np.float16)).to(dev)
+        e0 = torch.from_numpy(np.exp(1j * rng.uniform(0, 6, (512, 512))).astype(np.complex64)).to(dev)
+        ea, eb = e0.clone(), e0.clone()
+        corr.set_tensor_cores(True)
+        corr.apply(ea, dnc, s.dn_scale)
+        corr.check()
+        corr.set_tensor_cores(False)
+        corr.apply(eb, dnc, s.dn_scale)
+        torch.cuda.synchronize()
+        d = float(torch.linalg.vector_norm(ea - eb) / torch.linalg.vector_norm(eb - e0))
+        print(f"512^2 apply: tensor cores vs FP32 pipes, relative to the correction: {d:.2e}")
+        assert d <= 2e-2
+    finally:
+        corr.free()

@@ -77,3 +77,19 @@ def test_first_adam_step_moves_by_lr_sign_g():
     g = np.array([3.0, -0.2, 1e-3, -7.0])
     th, m, v = oc.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, 1e-3)
     assert np.allclose(th, -1e-3 * np.sign(g), rtol=1e-4)
+
+
+def test_bf16_rounding_of_the_inference_activations():
+    """round_bf16: representable values stay, ties go to the even neighbour,
+    and act_bf16=False leaves the forward pass unchanged."""
+    one_ulp = 2.0 ** -7                                       # bfloat16 spacing on [1, 2)
+    vals = np.array([1.0, 1.0 + one_ulp, 1.0 + one_ulp / 2, 1.0 + 3 * one_ulp / 2, -2.5, 0.0])
+    got = oc.round_bf16(vals)
+    assert np.array_equal(got, [1.0, 1.0 + one_ulp, 1.0, 1.0 + 2 * one_ulp, -2.5, 0.0])
+    rng = np.random.default_rng(9)
+    theta = rng.standard_normal(oc.param_count(2)) * 0.1
+    X = rng.standard_normal((1, 2, 8, 8))
+    a, _, _ = oc.forward(theta, X, 0.5)
+    b, _, _ = oc.forward(theta, X, 0.5, act_bf16=False)
+    c, _, _ = oc.forward(theta, X, 0.5, act_bf16=True)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
