@@ -164,15 +164,23 @@ using Rad8x8x3 = Radices<8, 8, 3>;
 using Rad3x8x8 = Radices<3, 8, 8>;
 using Rad8x8x6 = Radices<8, 8, 6>;
 using Rad6x8x8 = Radices<6, 8, 8>;
+using Rad8x8x4 = Radices<8, 8, 4>;
+using Rad4x8x8 = Radices<4, 8, 8>;
 
 template <int N>
 struct Cfg;
 template <> struct Cfg<64> : LoopCfg<64, 8, 8, 8, 73> {};
 template <> struct Cfg<128> : GroupCfg<128, 8, 145, GroupFFT<128, 8, 8, -1, Rad8x16>, GroupFFT<128, 8, 16, +1, Rad16x8>> {};
 template <> struct Cfg<192> : GroupCfg<192, 8, 219, GroupFFT<192, 8, 8, -1, Rad8x8x3>, GroupFFT<192, 8, 8, +1, Rad3x8x8>> {};
-template <> struct Cfg<256> : LoopCfg<256, 16, 16, 16, 273> {};
+// 256 and 512: one row per warp (32 threads, 8 or 16 points each), so a
+// single field spreads over 32 or 64 CTAs (about 1.4x and 1.7x shorter slices
+// than two rows per warp); 512 keeps the rolled radix-8 loop, whose small code
+// serves the batched kernel (where all sizes share one instruction stream)
+// better than an unrolled 16 x 16 x 2 schedule; strides from the half-warp
+// bank model
+template <> struct Cfg<256> : GroupCfg<256, 32, 274, GroupFFT<256, 32, 16, -1, Rad8x8x4>, GroupFFT<256, 32, 16, +1, Rad4x8x8>> {};
 template <> struct Cfg<384> : GroupCfg<384, 16, 409, GroupFFT<384, 16, 16, -1, Rad8x8x6>, GroupFFT<384, 16, 16, +1, Rad6x8x8>> {};
-template <> struct Cfg<512> : LoopCfg<512, 16, 8, 16, 545> {};
+template <> struct Cfg<512> : LoopCfg<512, 32, 8, 16, 546> {};
 template <> struct Cfg<1024> : FourStepCfg<LoopCfg<1024, 32, 32, 32, 1058>, 32> {};
 
 // shared memory of the half-step kernels: twiddle tables, then the buffers
