@@ -97,6 +97,27 @@ struct LoopCfg : CfgBase<N_, T_, GS_> {
     }
     conj_all(v, E::PTS);
   }
+  // The propagation step's hand-off from the column to the row half-step
+  // carries conjugated data, so that the conjugations around the inverse
+  // transforms fold into the neighbouring products.  Both half-steps are then
+  // NP forward passes, mid, NP forward passes: on the column side mid returns
+  // the conjugate of its product (the inverse of it is left conjugated for the
+  // row side); on the row side the first passes take the conjugated spectrum,
+  // so mid receives the conjugate of the inverse and returns the plain product
+  // for the forward transform.
+  template <class Mid>
+  __device__ __forceinline__ static void fwd_mid_fwd(float2* v, float2* buf, const float2* twf,
+                                                     const float2*, int t, Mid&& mid) {
+#pragma unroll 1
+    for (int q = 0; q < 2 * E::NP; ++q) {
+      if (q == E::NP) mid(v);
+      E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t);
+    }
+  }
+  // conjugated data in, conjugate of the inverse out
+  __device__ __forceinline__ static void inv_c(float2* v, float2* buf, const float2* twf, const float2*, int t) {
+    E::run_fwd(v, buf, twf, t);
+  }
 };
 
 template <int N_, int T_, int GS_, class F_, class I_>
@@ -193,14 +214,12 @@ __host__ __device__ constexpr int cfg_twiddles() {
   return C::TWF + C::TWI + C::TW4;
 }
 
-// exp(i x) for the phase screen.  For |x| <= 1/4 (|dn| <= 0.12 at the
-// paper's wavelengths and slice thicknesses) the Taylor series of sin and cos
-// truncated after x^7 and x^8 (truncation below 1.1e-11), for |x| <= pi/4
-// after x^11 and x^12 (truncation below 1e-11), both evaluated by Horner's
-// rule in x^2 (branch free); larger arguments use sincosf.  Callers pick the
-// evaluation once per warp (phasor_range) so that the loop over a row's
-// elements has no per-element branch and its independent elements can
-// interleave.
+// exp(i x) for the phase screen: the Taylor series of sin and cos evaluated
+// by Horner's rule in x^2 (branch free), for |x| <= pi/4 truncated after x^11
+// and x^12 (truncation below 1e-11), with a shorter form for |x| <= 1/8
+// below; larger arguments use sincosf.  Callers pick the evaluation once per
+// warp (phasor_range) so that the loop over a row's elements has no
+// per-element branch and its independent elements can interleave.
 constexpr float kPhasorPolyMax = 0.785398163f;
 
 __device__ __forceinline__ float2 unit_phasor_poly(float x) {
@@ -217,21 +236,55 @@ __device__ __forceinline__ float2 unit_phasor_poly(float x) {
   return make_float2(c, s);
 }
 
-constexpr float kPhasorSmallMax = 0.25f;
+constexpr float kPhasorTinyMax = 0.125f;
 
-__device__ __forceinline__ float2 unit_phasor_small(float x) {
+// The screen evaluates two phases at once with the packed two-lane FP32
+// operations of sm_100 and later (lane pair = two elements of a row): cos and
+// sin of x.x and x.y, returned as the pairs (cos, cos) and (sin, sin).
+// unit_phasor_tiny2 takes |x| <= 1/8 (Taylor series of sin and cos truncated
+// after x^5 and x^6: truncation below 1e-10, k0 |dn| dz <= 1/8 covers index
+// steps up to 0.06 at 0.1625 um slices and 0.5 um light); unit_phasor_poly2
+// is unit_phasor_poly on two lanes.
+__device__ __forceinline__ float2 pair(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ float2 unit_phasor_tiny(float x) {
   const float x2 = x * x;
-  const float ps = fmaf(fmaf(x2, -1.98412698e-4f, 8.33333333e-3f), x2, -1.66666667e-1f);
-  const float s = fmaf(ps, x2 * x, x);
-  const float c =
-      fmaf(fmaf(fmaf(fmaf(x2, 2.48015873e-5f, -1.38888889e-3f), x2, 4.16666667e-2f), x2, -0.5f), x2, 1.0f);
+  const float s = fmaf(fmaf(x2, 8.33333333e-3f, -1.66666667e-1f), x2 * x, x);
+  const float c = fmaf(fmaf(fmaf(x2, -1.38888889e-3f, 4.16666667e-2f), x2, -0.5f), x2, 1.0f);
   return make_float2(c, s);
+}
+
+__device__ __forceinline__ void unit_phasor_tiny2(float2 x, float2& c, float2& s) {
+  const float2 x2 = __fmul2_rn(x, x);
+  const float2 ps = __ffma2_rn(x2, pair(8.33333333e-3f), pair(-1.66666667e-1f));
+  s = __ffma2_rn(ps, __fmul2_rn(x2, x), x);
+  c = __ffma2_rn(__ffma2_rn(__ffma2_rn(x2, pair(-1.38888889e-3f), pair(4.16666667e-2f)), x2, pair(-0.5f)), x2,
+                 pair(1.0f));
+}
+
+__device__ __forceinline__ void unit_phasor_poly2(float2 x, float2& c, float2& s) {
+  const float2 x2 = __fmul2_rn(x, x);
+  float2 ps = __ffma2_rn(x2, pair(-2.50521084e-8f), pair(2.75573192e-6f));
+  ps = __ffma2_rn(ps, x2, pair(-1.98412698e-4f));
+  ps = __ffma2_rn(ps, x2, pair(8.33333333e-3f));
+  ps = __ffma2_rn(ps, x2, pair(-1.66666667e-1f));
+  s = __ffma2_rn(ps, __fmul2_rn(x2, x), x);
+  float2 pc = __ffma2_rn(x2, pair(2.08767570e-9f), pair(-2.75573192e-7f));
+  pc = __ffma2_rn(pc, x2, pair(2.48015873e-5f));
+  pc = __ffma2_rn(pc, x2, pair(-1.38888889e-3f));
+  pc = __ffma2_rn(pc, x2, pair(4.16666667e-2f));
+  pc = __ffma2_rn(pc, x2, pair(-0.5f));
+  c = __ffma2_rn(pc, x2, pair(1.0f));
 }
 
 __device__ __forceinline__ float2 unit_phasor_libm(float x) {
   float s, c;
   sincosf(x, &s, &c);
   return make_float2(c, s);
+}
+__device__ __forceinline__ void unit_phasor_libm2(float2 x, float2& c, float2& s) {
+  sincosf(x.x, &s.x, &c.x);
+  sincosf(x.y, &s.y, &c.y);
 }
 
 // exp(i x) for any moderate |x| without a branch: Cody-Waite reduction
@@ -254,7 +307,7 @@ __device__ __forceinline__ float2 unit_phasor_reduced(float x) {
 // |screen phase|: 0 the short polynomial, 1 the long one, 2 sincosf (NaN
 // index values keep a polynomial; they are reported separately).
 __device__ __forceinline__ int phasor_range(float max_abs_phase) {
-  if (__all_sync(0xffffffffu, !(max_abs_phase > kPhasorSmallMax))) return 0;
+  if (__all_sync(0xffffffffu, !(max_abs_phase > kPhasorTinyMax))) return 0;
   return __all_sync(0xffffffffu, !(max_abs_phase > kPhasorPolyMax)) ? 1 : 2;
 }
 
@@ -453,7 +506,7 @@ __device__ __forceinline__ void store_layout(const float2* v, float2* dst, int t
 // Rows [r0, r1) of the team member; each group of T threads takes one row per
 // round.  Groups without a row run the transforms on zeros (so that the warp
 // stays converged for __syncwarp) and skip all memory traffic.
-template <int N, int MODE, bool KAPPA = false>
+template <int N, int MODE, bool KAPPA = false, bool PK = true>
 __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1, int z, float2* s_buf,
                                               const float2* s_twf, const float2* s_twi, bool& bad,
                                               const Stage& st = Stage()) {
@@ -515,6 +568,10 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
       if (active && a.inten && z >= a.iz0 && z < a.iz1)
         irow = st.inten ? st.inten + (size_t)(row - r0) * N : a.inten + ((size_t)(z - a.iz0) * N + row) * N;
       const bool i_smem = st.inten != nullptr;
+      // LoopFFT sizes receive the conjugated spectrum from the column
+      // half-step (LoopCfg::fwd_mid_fwd): the screen multiplies conj(w)
+      constexpr bool CJ = C::kLoop;
+      auto scr = [](float2 w, float2 p) { return CJ ? cmul_conj_in(w, p) : cmul(w, p); };
       // phase screen exp(i k0 dn dz) and |E|^2 on the natural-order field;
       // the evaluation of the phasor (polynomial or sincosf) is chosen once per
       // warp so the element loop is branch free and its elements interleave
@@ -535,19 +592,41 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
         const float off = a.delta ? a.delta[z] : 0.f;
         const float c0 = -a.screen_c * off;
         const int range = phasor_range(a.screen_c * (mx + fabsf(off)));
-        auto body = [&](auto phasor) {
+        // PK: two elements per packed evaluation (single-instance kernels);
+        // the batched kernel, whose one instruction stream holds every size,
+        // measured faster with the scalar form
+        static_assert(!PK || C::PTS % 2 == 0, "the packed screen takes elements in pairs");
+        auto body2 = [&](auto phasor2) {
 #pragma unroll
-          for (int q = 0; q < C::PTS; ++q) {
-            const int x = layout_index<N, C::T, C::R0>(q, t);
+          for (int q = 0; q < C::PTS; q += 2) {
             // |E|^2 after the (unit-modulus) screen is |E|^2 before it, to the
             // phasor's rounding; taken first it does not wait for the phasor
+            if (irow) {
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int x = layout_index<N, C::T, C::R0>(q + u, t);
+                const float iv = fmaf(w[q + u].x, w[q + u].x, w[q + u].y * w[q + u].y);
+                if (i_smem) irow[x] = iv;
+                else __stcs(irow + x, iv);
+              }
+            }
+            float2 cs, sn;
+            phasor2(__ffma2_rn(pair(a.screen_c), make_float2(dval[q], dval[q + 1]), pair(c0)), cs, sn);
+            w[q] = scr(w[q], make_float2(cs.x, sn.x));
+            w[q + 1] = scr(w[q + 1], make_float2(cs.y, sn.y));
+          }
+        };
+        auto body1 = [&](auto phasor) {
+#pragma unroll
+          for (int q = 0; q < C::PTS; ++q) {
             const float2 wq = w[q];
             if (irow) {
+              const int x = layout_index<N, C::T, C::R0>(q, t);
               const float iv = fmaf(wq.x, wq.x, wq.y * wq.y);
               if (i_smem) irow[x] = iv;
               else __stcs(irow + x, iv);
             }
-            w[q] = cmul(wq, phasor(fmaf(a.screen_c, dval[q], c0)));
+            w[q] = scr(wq, phasor(fmaf(a.screen_c, dval[q], c0)));
           }
         };
         if constexpr (KAPPA) {
@@ -558,7 +637,7 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
             const int x = layout_index<N, C::T, C::R0>(q, t);
             const float kv = __half2float(__ldcs(skap + x));
             ksum += kv;
-            const float2 e = cmul(w[q], unit_phasor_reduced(fmaf(a.screen_c, dval[q], c0)));
+            const float2 e = scr(w[q], unit_phasor_reduced(fmaf(a.screen_c, dval[q], c0)));
             const float att = expf(-a.screen_c * kv);
             w[q] = make_float2(e.x * att, e.y * att);
             if (irow) {
@@ -569,13 +648,20 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
           }
           bad |= active && !isfinite(ksum);
         } else {
-          if (range == 0) body([](float ph) { return unit_phasor_small(ph); });
-          else if (range == 1) body([](float ph) { return unit_phasor_poly(ph); });
-          else body([](float ph) { return unit_phasor_libm(ph); });
+          if constexpr (PK) {
+            if (range == 0) body2([](float2 ph, float2& c, float2& sn) { unit_phasor_tiny2(ph, c, sn); });
+            else if (range == 1) body2([](float2 ph, float2& c, float2& sn) { unit_phasor_poly2(ph, c, sn); });
+            else body2([](float2 ph, float2& c, float2& sn) { unit_phasor_libm2(ph, c, sn); });
+          } else {
+            if (range == 0) body1([](float ph) { return unit_phasor_tiny(ph); });
+            else if (range == 1) body1([](float ph) { return unit_phasor_poly(ph); });
+            else body1([](float ph) { return unit_phasor_libm(ph); });
+          }
         }
       };
       if constexpr (MODE == ROW_LAST) {
-        C::inv(v, buf, s_twf, s_twi, t);
+        if constexpr (CJ) C::inv_c(v, buf, s_twf, s_twi, t);
+        else C::inv(v, buf, s_twf, s_twi, t);
         screen(v);
         if (active) {
 #pragma unroll
@@ -583,7 +669,8 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
           store_layout<N, C::T, C::R0>(v, a.work + (size_t)row * N, t);
         }
       } else {
-        C::inv_mid_fwd(v, buf, s_twf, s_twi, t, screen);
+        if constexpr (CJ) C::fwd_mid_fwd(v, buf, s_twf, s_twi, t, screen);
+        else C::inv_mid_fwd(v, buf, s_twf, s_twi, t, screen);
         if (active) store_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
       }
     }
@@ -635,22 +722,22 @@ __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int 
       }
     }
     four_step_fwd<N1, SA>(v, tw, xw, xr);
+    // conj(X H [exp(i delta G)]): the inverse FFT_y is the forward one of the
+    // conjugate, and its conjugated output goes to the row half-step as it is
     if (st.h) {
       const float2* h = st.h + (size_t)((on ? col : c0) - c0) * C::HS + ai;
 #pragma unroll
-      for (int k = 0; k < N1; ++k) v[k] = cmul(v[k], h[N1 * k]);
+      for (int k = 0; k < N1; ++k) v[k] = cmul_conj_out(v[k], h[N1 * k]);
     } else {
       const float2* h = a.ht + (size_t)(on ? col : c0) * N + ai;
 #pragma unroll
-      for (int k = 0; k < N1; ++k) v[k] = cmul(v[k], __ldg(h + N1 * k));
+      for (int k = 0; k < N1; ++k) v[k] = cmul_conj_out(v[k], __ldg(h + N1 * k));
     }
     if (a.delta) {
       const float* g = a.gt + (size_t)(on ? col : c0) * N + ai;
-      adapt_multiply<N1>(v, a.delta[z], [&](int k) { return __ldg(g + N1 * k); });
+      adapt_multiply<N1>(v, -a.delta[z], [&](int k) { return __ldg(g + N1 * k); });
     }
-    conj_all(v, N1);
     four_step_fwd<N1, SA>(v, tw, xw, xr);
-    conj_all(v, N1);
     if (on) {
       float2* dst = a.work + col;
 #pragma unroll
@@ -714,19 +801,26 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
     if constexpr (MODE == COL_PROP) {
       const float2* hcol = st.h ? st.h + (size_t)((active ? col : c0) - c0) * C::HS
                                 : a.ht + (size_t)(active ? col : c0) * N;
-      C::fwd_mid_inv(v, buf, s_twf, s_twi, t, [&](float2* w) {
+      // LoopFFT sizes hand the row half-step the conjugated inverse
+      // (LoopCfg::fwd_mid_fwd): mid returns conj(X H [exp(i delta G)])
+      constexpr bool CJ = C::kLoop;
+      auto prop = [&](float2* w) {
+        auto hm = [](float2 x, float2 h) { return CJ ? cmul_conj_out(x, h) : cmul(x, h); };
         if (st.h) {
 #pragma unroll
-          for (int q = 0; q < C::PTS; ++q) w[q] = cmul(w[q], hcol[layout_index<N, C::T, C::RL>(q, t)]);
+          for (int q = 0; q < C::PTS; ++q) w[q] = hm(w[q], hcol[layout_index<N, C::T, C::RL>(q, t)]);
         } else {
 #pragma unroll
-          for (int q = 0; q < C::PTS; ++q) w[q] = cmul(w[q], __ldg(hcol + layout_index<N, C::T, C::RL>(q, t)));
+          for (int q = 0; q < C::PTS; ++q) w[q] = hm(w[q], __ldg(hcol + layout_index<N, C::T, C::RL>(q, t)));
         }
         if (a.delta) {
           const float* g = a.gt + (size_t)(active ? col : c0) * N;
-          adapt_multiply<C::PTS>(w, a.delta[z], [&](int q) { return __ldg(g + layout_index<N, C::T, C::RL>(q, t)); });
+          adapt_multiply<C::PTS>(w, CJ ? -a.delta[z] : a.delta[z],
+                                 [&](int q) { return __ldg(g + layout_index<N, C::T, C::RL>(q, t)); });
         }
-      });
+      };
+      if constexpr (CJ) C::fwd_mid_fwd(v, buf, s_twf, s_twi, t, prop);
+      else C::fwd_mid_inv(v, buf, s_twf, s_twi, t, prop);
     } else {
       // focusing filter: exp(-i kz zf) / (n n) inside the pupil, 0 outside;
       // membership decided in FP64 with the same operation order as the oracle
@@ -1176,8 +1270,8 @@ __device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int
   for (int z = a.z_begin; z < a.z_end; ++z) {
     col_half_step<N, COL_PROP>(a, lo, hi, z, s_buf, s_twf, s_twi);
     cluster_sync_all();
-    if (z + 1 < a.z_end) row_half_step<N, ROW_STEP>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
-    else row_half_step<N, ROW_LAST>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+    if (z + 1 < a.z_end) row_half_step<N, ROW_STEP, false, false>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+    else row_half_step<N, ROW_LAST, false, false>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
     cluster_sync_all();
   }
 }
