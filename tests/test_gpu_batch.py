@@ -123,3 +123,23 @@ def test_seeded_batch_instances_with_their_inputs(B):
             assert intensity_rel_max(ig.cpu().numpy(), Ir) <= INTENSITY_TOL
     finally:
         B.bpm_free(plan)
+
+
+def test_batch_every_phasor_form(B):
+    """The batched kernel's screen (scalar form) with index steps that need
+    each phasor evaluation: small steps, steps up to 0.5 rad, and rows of
+    steps up to +-1.4 rad next to rows of small ones."""
+    cases = []
+    for k, n in enumerate([128, 256, 512, 192]):
+        rng = np.random.default_rng(300 + k)
+        dn = np.empty((3, n, n))
+        dn[0] = rng.uniform(0.0, 0.05, size=(n, n))
+        dn[1] = rng.uniform(0.0, 0.4, size=(n, n))
+        dn[2] = rng.uniform(-1.1, 1.1, size=(n, n))
+        dn[2, ::3] = rng.uniform(0.0, 0.05, size=dn[2, ::3].shape)
+        cases.append((n, 3, 0.1, dn.astype(np.float16), bandlimited_field(n, 0.1, 0.85, 400 + k)))
+    E, I = _run_batch(B, cases)
+    for (n, nz, d, dn16, E0), Eg, Ig in zip(cases, E, I):
+        Er, Ir = oracle.bpm(inputs.dn_to_f64(dn16), E0, d, d, d, 0.5, 1.33)
+        assert field_rel_l2(Eg, Er) <= FIELD_TOL / 10, n
+        assert intensity_rel_max(Ig, Ir) <= INTENSITY_TOL / 10, n

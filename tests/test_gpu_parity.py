@@ -63,6 +63,32 @@ def test_every_size_random_inputs(B, n, flags):
     assert intensity_rel_max(Ig, Ir) <= INTENSITY_TOL / 10
 
 
+@pytest.mark.parametrize("n", [64, 128, 192, 256, 384, 512, 1024])
+def test_every_size_every_phasor_form(B, n):
+    """The screen picks its phasor per warp from the largest |k0 dn dz| of the
+    warp's elements: the short series (<= 1/8), the long one (<= pi/4) or
+    sincosf.  Slice 0 stays in the first, slice 1 reaches the second, slice 2
+    mixes rows of small steps with rows of steps up to +-1.4 rad, negative
+    ones included, so that warps of every form (and warps whose rows need
+    different forms) meet in one propagation."""
+    nz, d = 3, 0.1
+    rng = np.random.default_rng(7 * n + 1)
+    dn = np.empty((nz, n, n))
+    dn[0] = rng.uniform(0.0, 0.05, size=(n, n))
+    dn[1] = rng.uniform(0.0, 0.4, size=(n, n))
+    dn[2] = rng.uniform(-1.1, 1.1, size=(n, n))
+    dn[2, ::3] = rng.uniform(0.0, 0.05, size=dn[2, ::3].shape)
+    dn16 = dn.astype(np.float16)
+    k0dz = 2 * np.pi / 0.5 * d
+    ph = np.abs(dn16.astype(np.float64)) * k0dz
+    assert ph[0].max() <= 0.125 and 0.125 < ph[1].max() <= np.pi / 4 and ph[2].max() > np.pi / 4
+    E0 = bandlimited_field(n, d, 0.9, n + 3)
+    Eg, Ig = run_gpu(B, dn16, E0, d)
+    Er, Ir = oracle.bpm(inputs.dn_to_f64(dn16), E0, d, d, d, 0.5, 1.33)
+    assert field_rel_l2(Eg, Er) <= FIELD_TOL / 10
+    assert intensity_rel_max(Ig, Ir) <= INTENSITY_TOL / 10
+
+
 def test_multiplex_synthesis_1024(B):
     w = inputs.multiplex_1024(nz=64)
     f = w.foci()
