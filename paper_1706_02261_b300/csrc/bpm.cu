@@ -58,9 +58,12 @@ bool supported_n(int n) {
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Host-built twiddle table of one transform (FP64, rounded once): for every
-// pass p >= 1 of the radix list, N entries laid out [b][r][t] holding
-// W_{Ns R}^{(j mod Ns) r}, j = t + b T, with the transform's sign.
-void append_twiddles(std::vector<float2>& out, int N, int T, const std::vector<int>& radices, int sign) {
+// pass p >= 1 of the radix list, N entries holding W_{Ns R}^{(j mod Ns) r},
+// j = t + b T, with the transform's sign, laid out [b][r][t], or with
+// `paired` (LoopFFT, even R) [b][r/2][t][r%2] so that a thread reads the
+// twiddles of r and r + 1 with one 16-byte load.
+void append_twiddles(std::vector<float2>& out, int N, int T, const std::vector<int>& radices, int sign,
+                     bool paired = false) {
   int Ns = 1;
   for (size_t p = 0; p < radices.size(); ++p) {
     const int R = radices[p];
@@ -74,7 +77,9 @@ void append_twiddles(std::vector<float2>& out, int N, int T, const std::vector<i
             const int j = t + b * T;
             const long long e = (long long)(j % Ns) * r % (long long)(Ns * R);
             const double ang = sign * kTwoPi * (double)e / (double)(Ns * R);
-            out[base + (size_t)(b * R + r) * T + t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            const size_t at = paired ? ((size_t)(b * (R / 2) + r / 2) * T + t) * 2 + (r & 1)
+                                     : (size_t)(b * R + r) * T + t;
+            out[base + at] = make_float2((float)std::cos(ang), (float)std::sin(ang));
           }
     }
     Ns *= R;
@@ -93,20 +98,22 @@ std::vector<float2> twiddles_for() {
   using C = Cfg<N>;
   std::vector<float2> v;
   if constexpr (C::kLoop) {
-    append_twiddles(v, N, C::T, std::vector<int>(C::E::NP, C::E::R), -1);
+    append_twiddles(v, N, C::T, std::vector<int>(C::E::NP, C::E::R), -1, true);
   } else {
     append_twiddles(v, N, C::T, radix_list<typename C::F::Rad>(), -1);
     append_twiddles(v, N, C::T, radix_list<typename C::I::Rad>(), +1);
   }
   if constexpr (C::TW4 > 0) {
-    // four-step column transform: W_N^(a k) at [k N1 + a], forward sign
+    // four-step column transform: W_N^(a k), forward sign, laid out
+    // [k/2][a][k%2] (the twiddles of k and k + 1 in one 16-byte load)
     const int N1 = C::FS_N1;
-    for (int k = 0; k < N1; ++k)
-      for (int a = 0; a < N1; ++a) {
-        const long long e = (long long)a * k % N;
-        const double ang = -kTwoPi * (double)e / (double)N;
-        v.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
-      }
+    for (int kp = 0; kp < N1 / 2; ++kp)
+      for (int a = 0; a < N1; ++a)
+        for (int k = 2 * kp; k < 2 * kp + 2; ++k) {
+          const long long e = (long long)a * k % N;
+          const double ang = -kTwoPi * (double)e / (double)N;
+          v.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+        }
   }
   return v;
 }

@@ -174,7 +174,7 @@ struct FourStepCfg : Base {
   static constexpr int FS_N1 = N1;
   static constexpr int FS_SA = (N1 + 15) / 16 * 16 + 1;
   static constexpr int FS_SC = N1 * FS_SA + ((16 / Base::NG) % 16 - (N1 * FS_SA) % 16 + 16) % 16;
-  static constexpr int TW4 = Base::N;       // W_N^(a k) at [k N1 + a]
+  static constexpr int TW4 = Base::N;       // W_N^(a k) at [k/2][a][k%2]
   static constexpr int BUFLEN = Base::NG * FS_SC > Base::NG * Base::GS ? Base::NG * FS_SC : Base::NG * Base::GS;
   static constexpr int HS = Base::N + 16 / Base::NG;
 };
@@ -678,16 +678,21 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
 }
 
 // One forward four-step transform of the columns held as in FourStepCfg:
-// N1-point DFT over the registers, twiddles W_N^(a k) (tw = table + a, read
-// with stride N1: the NG threads of a row share each value), exchange
+// N1-point DFT over the registers, twiddles W_N^(a k) (tw = pair table + a,
+// the pair of k = 2 kp, 2 kp + 1 at stride N1: the NG threads of a row share
+// each value), exchange
 // (xw: this thread's row of its column block, xr: its column, stride SA),
 // N1-point DFT.  Two CTA barriers: the buffer is free before it is written,
 // and complete before it is read.
 template <int N1, int SA>
-__device__ __forceinline__ void four_step_fwd(float2* v, const float2* tw, float2* xw, const float2* xr) {
+__device__ __forceinline__ void four_step_fwd(float2* v, const float4* tw, float2* xw, const float2* xr) {
   Dft<N1, -1>::run(v);
 #pragma unroll
-  for (int k = 1; k < N1; ++k) v[k] = cmul(v[k], tw[k * N1]);
+  for (int kp = 0; kp < N1 / 2; ++kp) {
+    const float4 w = tw[kp * N1];
+    if (kp > 0) v[2 * kp] = cmul(v[2 * kp], make_float2(w.x, w.y));
+    v[2 * kp + 1] = cmul(v[2 * kp + 1], make_float2(w.z, w.w));
+  }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < N1; ++k) xw[k] = v[k];
@@ -706,7 +711,8 @@ __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int 
   using C = Cfg<N>;
   constexpr int N1 = C::FS_N1, NG = C::NG, SA = C::FS_SA, SC = C::FS_SC;
   const int c = threadIdx.x % NG, ai = threadIdx.x / NG;
-  const float2* tw = s_tw4 + ai;
+  // [k/2][a][k%2] pairs (16-byte aligned: the table follows whole tables)
+  const float4* tw = reinterpret_cast<const float4*>(s_tw4) + ai;
   float2* xw = s_buf + c * SC + ai * SA;
   const float2* xr = s_buf + c * SC + ai;
   for (int cb = c0; cb < c1; cb += NG) {

@@ -350,7 +350,7 @@ struct LoopFFT {
   static constexpr int B = N / (R * T);
   static constexpr int BUF = N + N / PAD;
   static constexpr int TW = (NP - 1) * N;
-  static_assert((1 << LGR) == R, "radix must be a power of two");
+  static_assert((1 << LGR) == R && R >= 2, "radix must be a power of two (even: paired twiddles)");
   static_assert(B * R * T == N && B >= 1, "each thread must own whole butterflies");
   static_assert((T <= 32 && 32 % T == 0) || T % 32 == 0, "a group is part of one warp or whole warps");
 
@@ -360,11 +360,17 @@ struct LoopFFT {
   __device__ __forceinline__ static void pass(int p, float2* v, float2* buf, const float2* tw, int t,
                                               int bar_id = 0) {
     if (p > 0) {
-      const float2* twp = tw + (p - 1) * N;
+      // table [pass][b][r/2][t][r%2]: the twiddles of r and r + 1 in one
+      // 16-byte load (the table starts 16-byte aligned)
+      const float4* twp = reinterpret_cast<const float4*>(tw + (p - 1) * N);
 #pragma unroll
       for (int b = 0; b < B; ++b)
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], twp[(b * R + r) * T + t]);
+        for (int rp = 0; rp < R / 2; ++rp) {
+          const float4 w = twp[(b * (R / 2) + rp) * T + t];
+          if (rp > 0) v[b * R + 2 * rp] = cmul(v[b * R + 2 * rp], make_float2(w.x, w.y));
+          v[b * R + 2 * rp + 1] = cmul(v[b * R + 2 * rp + 1], make_float2(w.z, w.w));
+        }
     }
 #pragma unroll
     for (int b = 0; b < B; ++b) Dft<R, -1>::run(v + b * R);
