@@ -282,16 +282,29 @@ const char *bpm_last_error(void);
 /* bpm_plan_info - launch configuration chosen for the plan, for reports:
  * out[0] = team CTAs, out[1] = threads per CTA, out[2] = dynamic shared
  * memory bytes, out[3] = persistent (1) or multi-launch (0), out[4] = kernel
- * launches per bpm_propagate call. */
+ * launches per bpm_propagate call, out[5] = transform schedule in use,
+ * out[6] = number of schedules of the plan's grid size (single-field plans;
+ * batched plans report 0 and 1).  n_out may be smaller than 7. */
 int bpm_plan_info(bpm_plan_t p, int *out, int n_out);
 
-/* bpm_autotune - batched plans: time the propagation of slices [0, z_probe)
- * of every instance with each cluster size (2, 4, 8, 16 CTAs per team) on the
- * given buffers and keep the fastest for later calls.  Overwrites d_Eout and
- * the first z_probe intensity slices; synchronises the stream.  A no-op for
- * single-instance plans.  Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
+/* bpm_autotune - time the propagation of slices [0, z_probe) on the given
+ * buffers and keep the fastest configuration for later calls.  Batched plans:
+ * every instance with each cluster size (2, 4, 8, 16 CTAs per team).
+ * Single-field plans: each transform schedule of the grid size (radix order
+ * and pass structure of the row and column transforms: 256 and 512 have three,
+ * 1024 two, the other sizes one).  Overwrites d_Eout and the first z_probe
+ * intensity slices; synchronises the stream (and the device when the
+ * schedule changes).  Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
 int bpm_autotune(bpm_plan_t p, const void *const *d_dn, const void *const *d_Ein, void *const *d_Eout,
                  float *const *d_I, int z_probe, cudaStream_t stream);
+
+/* bpm_set_schedule - single-field plans: use transform schedule `schedule`
+ * (0 .. out[6] - 1 of bpm_plan_info; a plan starts with the schedule measured
+ * fastest for its size, 2 for 512 and 0 for the others).
+ * Results of every schedule agree to FP32 rounding.  Synchronises the device
+ * when the schedule changes.  Errors: BPM_ERR_ARG (NULL plan, schedule out of
+ * range), BPM_ERR_UNSUPPORTED (batched plan), BPM_ERR_CUDA. */
+int bpm_set_schedule(bpm_plan_t p, int schedule);
 
 /* bpm_debug_set_barrier_timeout - test hook: device barrier wait limit in
  * nanoseconds for this plan (default 2e9), and an extra count added to the

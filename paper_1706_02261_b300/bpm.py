@@ -65,6 +65,7 @@ _lib.bpm_last_error.restype = ctypes.c_char_p
 _lib.bpm_plan_info.argtypes = [_vp, ctypes.POINTER(_i), _i]
 _lib.bpm_debug_set_barrier_timeout.argtypes = [_vp, ctypes.c_ulonglong, _u]
 _lib.bpm_autotune.argtypes = [_vp, _pp, _pp, _pp, _pp, _i, _vp]
+_lib.bpm_set_schedule.argtypes = [_vp, _i]
 _lib.bpm_propagate_host.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _i, _vp]
 _lib.bpm_propagate_static.argtypes = [ctypes.POINTER(bpm_instance_desc), _vp, _vp, _vp, _vp, _i, _i, _vp]
 _lib.bpm_propagate_window.argtypes = [_vp, _pp, _pp, _pp, _pp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), _vp]
@@ -73,7 +74,8 @@ _lib.bpm_phase_conjugate.argtypes = [_vp, _i, _vp, _vp]
 _lib.bpm_propagate_absorbing.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp]
 _lib.bpm_demultiplex.argtypes = [_vp, _i, _vp, _i, _i, _i, ctypes.POINTER(_i), _i, _i, _i, _vp, _vp]
 for _f in ("bpm_plan", "bpm_propagate", "bpm_multiplex_psf", "bpm_light_sheet", "bpm_check",
-           "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout", "bpm_propagate_static", "bpm_autotune", "bpm_propagate_host"):
+           "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout", "bpm_propagate_static", "bpm_autotune", "bpm_propagate_host",
+           "bpm_set_schedule"):
     getattr(_lib, _f).restype = _i
 
 
@@ -220,7 +222,12 @@ def bpm_propagate_host(plan, dn_host, e_in, e_out_host, inten_host=None, chunk: 
 
 
 def bpm_autotune(plan, dn, e_in, e_out, inten=None, z_probe: int = 8, stream=None) -> int:
-    """Pick the fastest cluster size of a batched plan on these buffers (lists, one entry per instance)."""
+    """Pick the fastest configuration on these buffers: the cluster size of a
+    batched plan (lists, one entry per instance) or the transform schedule of a
+    single-field plan (tensors or one-entry lists)."""
+    if not isinstance(e_in, (list, tuple)):
+        dn, e_in, e_out = [dn], [e_in], [e_out]
+        inten = [inten] if inten is not None else None
     a_dn = _arr([_ptr(t) for t in dn])
     a_in = _arr([_ptr(t) for t in e_in])
     a_out = _arr([_ptr(t) for t in e_out])
@@ -262,10 +269,15 @@ def bpm_free(plan) -> int:
 
 
 def bpm_plan_info(plan) -> dict:
-    out = (ctypes.c_int * 5)()
-    _check(_lib.bpm_plan_info(plan, out, 5))
+    out = (ctypes.c_int * 7)()
+    _check(_lib.bpm_plan_info(plan, out, 7))
     return {"team_ctas": out[0], "threads": out[1], "smem_bytes": out[2], "persistent": out[3],
-            "launches_per_call": out[4]}
+            "launches_per_call": out[4], "schedule": out[5], "schedules": out[6]}
+
+
+def bpm_set_schedule(plan, schedule: int) -> int:
+    """Transform schedule of a single-field plan (0 .. plan_info()['schedules'] - 1)."""
+    return _check(_lib.bpm_set_schedule(plan, schedule))
 
 
 def bpm_debug_set_barrier_timeout(plan, timeout_ns: int, extra_arrivals: int = 0) -> int:

@@ -93,9 +93,9 @@ std::vector<int> radix_list() {
   return r;
 }
 
-template <int N>
+template <int N, int S = 0>
 std::vector<float2> twiddles_for() {
-  using C = Cfg<N>;
+  using C = Cfg<N, S>;
   std::vector<float2> v;
   if constexpr (C::kLoop) {
     append_twiddles(v, N, C::T, std::vector<int>(C::E::NP, C::E::R), -1, true);
@@ -124,6 +124,7 @@ struct NRes {
   int n = 0;
   float2* tw = nullptr;
   float2* tmp = nullptr;    // N x N scratch for input synthesis (allocated on first use)
+  int sched = 0;            // transform schedule (Cfg<n, sched>)
   int team = 0;             // CTAs per field
   size_t smem = 0;          // dynamic shared memory of the half-step kernels
   size_t smem_persist = 0;  // ... of the persistent kernel (with its staging buffers)
@@ -177,20 +178,20 @@ struct bpm_plan_s {
 
 namespace {
 
-template <int N>
+template <int N, int S>
 int setup_kernels(NRes& r, int sms) {
-  using C = Cfg<N>;
+  using C = Cfg<N, S>;
   r.smem = cfg_smem_bytes<C>();
   const int smem = (int)r.smem;
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_STEP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_LAST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_INV_ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_col_kernel<N, COL_PROP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_col_kernel<N, COL_FOCUS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_light_sheet_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_FWD, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_STEP, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_LAST, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_STEP, true, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_LAST, true, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_INV_ACC, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_col_kernel<N, COL_PROP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_col_kernel<N, COL_FOCUS, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPM_CU(cudaFuncSetAttribute(bpm_light_sheet_kernel<N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               smem + (int)(C::GS * sizeof(float2))));
   // smallest team that gives every group one row per half-step, at most one
   // CTA per SM; with the four-step column layout every SM takes rows (fewer
@@ -213,32 +214,39 @@ int setup_kernels(NRes& r, int sms) {
   if (r.smem + db + ib > budget) r.i_stage = 0;
   if (r.smem + db > budget) r.dn_stage = 0;
   r.smem_persist = r.smem + (r.h_res ? hb : 0) + (r.dn_stage ? db : 0) + (r.i_stage ? ib : 0);
-  BPM_CU(cudaFuncSetAttribute(bpm_persistent_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  BPM_CU(cudaFuncSetAttribute(bpm_persistent_kernel<N, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)r.smem_persist));
-  BPM_CU(cudaFuncSetAttribute((bpm_persistent_kernel<N, true>), cudaFuncAttributeMaxDynamicSharedMemorySize,
+  BPM_CU(cudaFuncSetAttribute((bpm_persistent_kernel<N, true, S>), cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)r.smem_persist));
   int per_sm = 0;
-  BPM_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpm_persistent_kernel<N>, kThreads,
+  BPM_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpm_persistent_kernel<N, false, S>, kThreads,
                                                        r.smem_persist));
   if (per_sm < 1) return fail(BPM_ERR_UNSUPPORTED, "persistent kernel for N=%d does not fit on an SM", N);
-  std::vector<float2> tw = twiddles_for<N>();
+  std::vector<float2> tw = twiddles_for<N, S>();
   if (tw.size() != (size_t)cfg_twiddles<C>() || tw.empty())
     return fail(BPM_ERR_UNSUPPORTED, "twiddle table size mismatch for N=%d", N);
+  r.sched = S;
   BPM_CU(cudaMalloc(&r.tw, tw.size() * sizeof(float2)));
   BPM_CU(cudaMemcpy(r.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
   return BPM_OK;
 }
 
-int setup_n(NRes& r, int n, int sms) {
+int setup_n(NRes& r, int n, int sms, int sched = 0) {
   r.n = n;
-  switch (n) {
-    case 64: return setup_kernels<64>(r, sms);
-    case 128: return setup_kernels<128>(r, sms);
-    case 192: return setup_kernels<192>(r, sms);
-    case 256: return setup_kernels<256>(r, sms);
-    case 384: return setup_kernels<384>(r, sms);
-    case 512: return setup_kernels<512>(r, sms);
-    case 1024: return setup_kernels<1024>(r, sms);
+  if (sched < 0 || sched >= kSchedules(n)) return fail(BPM_ERR_ARG, "size %d has no schedule %d", n, sched);
+  switch (n * 4 + sched) {
+    case 64 * 4: return setup_kernels<64, 0>(r, sms);
+    case 128 * 4: return setup_kernels<128, 0>(r, sms);
+    case 192 * 4: return setup_kernels<192, 0>(r, sms);
+    case 256 * 4: return setup_kernels<256, 0>(r, sms);
+    case 256 * 4 + 1: return setup_kernels<256, 1>(r, sms);
+    case 256 * 4 + 2: return setup_kernels<256, 2>(r, sms);
+    case 384 * 4: return setup_kernels<384, 0>(r, sms);
+    case 512 * 4: return setup_kernels<512, 0>(r, sms);
+    case 512 * 4 + 1: return setup_kernels<512, 1>(r, sms);
+    case 512 * 4 + 2: return setup_kernels<512, 2>(r, sms);
+    case 1024 * 4: return setup_kernels<1024, 0>(r, sms);
+    case 1024 * 4 + 1: return setup_kernels<1024, 1>(r, sms);
   }
   return fail(BPM_ERR_UNSUPPORTED, "grid size %d is not supported", n);
 }
@@ -252,6 +260,25 @@ int check_desc(const bpm_instance_desc& d, int i) {
   if (!(d.dx > 0) || !(d.dy > 0) || !(d.dz > 0) || !(d.lambda > 0) || !(d.n0 > 0) || !std::isfinite(d.dx) ||
       !std::isfinite(d.dy) || !std::isfinite(d.dz) || !std::isfinite(d.lambda) || !std::isfinite(d.n0))
     return fail(BPM_ERR_ARG, "instance %d: dx, dy, dz, lambda and n0 must be positive and finite", i);
+  return BPM_OK;
+}
+
+// Rebuild the per-size resources of a single-field plan for schedule sched
+// (twiddle table and launch configuration; the propagator tables and the
+// synthesis scratch do not depend on it).
+int switch_schedule(bpm_plan_s* p, int sched) {
+  NRes& cur = p->res.begin()->second;
+  if (cur.sched == sched) return BPM_OK;
+  NRes r;
+  int rc = setup_n(r, cur.n, p->sms, sched);
+  if (rc) {
+    cudaFree(r.tw);
+    return rc;
+  }
+  BPM_CU(cudaDeviceSynchronize());      // no launch of this plan may still read the old table
+  cudaFree(cur.tw);
+  r.tmp = cur.tmp;
+  cur = r;
   return BPM_OK;
 }
 
@@ -316,21 +343,21 @@ StepArgs base_args(bpm_plan_s* p, const InstPlan& in, const NRes& r) {
 
 // ---- launches ---------------------------------------------------------------
 
-template <int N>
+template <int N, int S>
 int launch_propagate(bpm_plan_s* p, const NRes& r, StepArgs a, cudaStream_t s) {
   const int G = r.team;
   if (p->flags & BPM_FLAG_MULTI_LAUNCH) {
-    bpm_row_kernel<N, ROW_FWD><<<G, kThreads, r.smem, s>>>(a, a.z_begin);
+    bpm_row_kernel<N, ROW_FWD, false, S><<<G, kThreads, r.smem, s>>>(a, a.z_begin);
     for (int zi = a.z_begin; zi < a.z_end; ++zi) {
       const int z = a.reverse ? a.z_begin + a.z_end - 1 - zi : zi;     // slice crossed by this step
-      bpm_col_kernel<N, COL_PROP><<<G, kThreads, r.smem, s>>>(a, z);
+      bpm_col_kernel<N, COL_PROP, S><<<G, kThreads, r.smem, s>>>(a, z);
       const bool last = zi + 1 == a.z_end;
       if (a.kappa) {
-        if (!last) bpm_row_kernel<N, ROW_STEP, true><<<G, kThreads, r.smem, s>>>(a, z);
-        else bpm_row_kernel<N, ROW_LAST, true><<<G, kThreads, r.smem, s>>>(a, z);
+        if (!last) bpm_row_kernel<N, ROW_STEP, true, S><<<G, kThreads, r.smem, s>>>(a, z);
+        else bpm_row_kernel<N, ROW_LAST, true, S><<<G, kThreads, r.smem, s>>>(a, z);
       } else {
-        if (!last) bpm_row_kernel<N, ROW_STEP><<<G, kThreads, r.smem, s>>>(a, z);
-        else bpm_row_kernel<N, ROW_LAST><<<G, kThreads, r.smem, s>>>(a, z);
+        if (!last) bpm_row_kernel<N, ROW_STEP, false, S><<<G, kThreads, r.smem, s>>>(a, z);
+        else bpm_row_kernel<N, ROW_LAST, false, S><<<G, kThreads, r.smem, s>>>(a, z);
       }
     }
     BPM_CU(cudaGetLastError());
@@ -338,50 +365,56 @@ int launch_propagate(bpm_plan_s* p, const NRes& r, StepArgs a, cudaStream_t s) {
   }
   BPM_CU(cudaMemsetAsync(p->bar, 0, sizeof(unsigned), s));
   void* args[] = {&a};
-  const void* fn = a.kappa ? (const void*)bpm_persistent_kernel<N, true> : (const void*)bpm_persistent_kernel<N>;
+  const void* fn = a.kappa ? (const void*)bpm_persistent_kernel<N, true, S> : (const void*)bpm_persistent_kernel<N, false, S>;
   BPM_CU(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args, r.smem_persist, s));
   return BPM_OK;
 }
 
-template <int N>
+template <int N, int S>
 int launch_synth_group(bpm_plan_s*, const NRes& r, StepArgs a, cudaStream_t s) {
   const int G = r.team;
-  bpm_row_kernel<N, ROW_FWD><<<G, kThreads, r.smem, s>>>(a, 0);
-  bpm_col_kernel<N, COL_FOCUS><<<G, kThreads, r.smem, s>>>(a, 0);
-  bpm_row_kernel<N, ROW_INV_ACC><<<G, kThreads, r.smem, s>>>(a, 0);
+  bpm_row_kernel<N, ROW_FWD, false, S><<<G, kThreads, r.smem, s>>>(a, 0);
+  bpm_col_kernel<N, COL_FOCUS, S><<<G, kThreads, r.smem, s>>>(a, 0);
+  bpm_row_kernel<N, ROW_INV_ACC, false, S><<<G, kThreads, r.smem, s>>>(a, 0);
   BPM_CU(cudaGetLastError());
   return BPM_OK;
 }
 
-template <int N>
+template <int N, int S>
 int launch_light_sheet(bpm_plan_s* p, const NRes& r, StepArgs a, double w0, double xc, cudaStream_t s) {
-  using C = Cfg<N>;
+  using C = Cfg<N, S>;
   const int grid = std::max(1, std::min(p->sms, (N * N + 4 * kThreads - 1) / (4 * kThreads)));
-  bpm_light_sheet_kernel<N><<<grid, kThreads, r.smem + C::GS * sizeof(float2), s>>>(a, w0, xc);
+  bpm_light_sheet_kernel<N, S><<<grid, kThreads, r.smem + C::GS * sizeof(float2), s>>>(a, w0, xc);
   BPM_CU(cudaGetLastError());
   return BPM_OK;
 }
 
-#define BPM_DISPATCH(n, call)                               \
-  switch (n) {                                              \
-    case 64: { constexpr int N = 64; return call; }         \
-    case 128: { constexpr int N = 128; return call; }       \
-    case 192: { constexpr int N = 192; return call; }       \
-    case 256: { constexpr int N = 256; return call; }       \
-    case 384: { constexpr int N = 384; return call; }       \
-    case 512: { constexpr int N = 512; return call; }       \
-    case 1024: { constexpr int N = 1024; return call; }     \
-  }                                                         \
-  return fail(BPM_ERR_UNSUPPORTED, "grid size %d is not supported", n);
+// call with the size N and schedule S of r as compile-time constants
+#define BPM_DISPATCH(r, call)                                                 \
+  switch ((r).n * 4 + (r).sched) {                                            \
+    case 64 * 4: { constexpr int N = 64, S = 0; return call; }                \
+    case 128 * 4: { constexpr int N = 128, S = 0; return call; }              \
+    case 192 * 4: { constexpr int N = 192, S = 0; return call; }              \
+    case 256 * 4: { constexpr int N = 256, S = 0; return call; }              \
+    case 256 * 4 + 1: { constexpr int N = 256, S = 1; return call; }          \
+    case 256 * 4 + 2: { constexpr int N = 256, S = 2; return call; }          \
+    case 384 * 4: { constexpr int N = 384, S = 0; return call; }              \
+    case 512 * 4: { constexpr int N = 512, S = 0; return call; }              \
+    case 512 * 4 + 1: { constexpr int N = 512, S = 1; return call; }          \
+    case 512 * 4 + 2: { constexpr int N = 512, S = 2; return call; }          \
+    case 1024 * 4: { constexpr int N = 1024, S = 0; return call; }            \
+    case 1024 * 4 + 1: { constexpr int N = 1024, S = 1; return call; }        \
+  }                                                                           \
+  return fail(BPM_ERR_UNSUPPORTED, "grid size %d (schedule %d) is not supported", (r).n, (r).sched);
 
 int dispatch_propagate(bpm_plan_s* p, const NRes& r, const StepArgs& a, cudaStream_t s) {
-  BPM_DISPATCH(r.n, launch_propagate<N>(p, r, a, s))
+  BPM_DISPATCH(r, (launch_propagate<N, S>(p, r, a, s)))
 }
 int dispatch_synth(bpm_plan_s* p, const NRes& r, const StepArgs& a, cudaStream_t s) {
-  BPM_DISPATCH(r.n, launch_synth_group<N>(p, r, a, s))
+  BPM_DISPATCH(r, (launch_synth_group<N, S>(p, r, a, s)))
 }
 int dispatch_light_sheet(bpm_plan_s* p, const NRes& r, const StepArgs& a, double w0, double xc, cudaStream_t s) {
-  BPM_DISPATCH(r.n, launch_light_sheet<N>(p, r, a, w0, xc, s))
+  BPM_DISPATCH(r, (launch_light_sheet<N, S>(p, r, a, w0, xc, s)))
 }
 
 int finish_call(bpm_plan_s* p, cudaStream_t s) {
@@ -571,7 +604,7 @@ extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_in
     const int n = inst[i].nx;
     if (!p->res.count(n)) {
       NRes r;
-      rc = setup_n(r, n, p->sms);
+      rc = setup_n(r, n, p->sms, n_inst == 1 ? kDefaultSchedule(n) : 0);
       p->res[n] = r;
       if (rc) break;
     }
@@ -910,14 +943,17 @@ extern "C" int bpm_plan_info(bpm_plan_t p, int* out, int n_out) {
   const NRes& r = p->res.begin()->second;
   const bool multi = (p->flags & BPM_FLAG_MULTI_LAUNCH) != 0;
   const int nz = p->inst[0].d.nz;
-  int vals[5] = {r.team, kThreads, (int)(multi ? r.smem : r.smem_persist), multi ? 0 : 1, multi ? 1 + 2 * nz : 1};
+  int vals[7] = {r.team, kThreads, (int)(multi ? r.smem : r.smem_persist), multi ? 0 : 1, multi ? 1 + 2 * nz : 1,
+                 r.sched, kSchedules(r.n)};
   if (p->inst.size() > 1) {
     vals[0] = p->cluster;
     vals[2] = (int)p->batch_smem;
     vals[3] = 1;
     vals[4] = 1;
+    vals[5] = 0;
+    vals[6] = 1;
   }
-  for (int i = 0; i < n_out && i < 5; ++i) out[i] = vals[i];
+  for (int i = 0; i < n_out && i < 7; ++i) out[i] = vals[i];
   return BPM_OK;
 }
 
@@ -996,11 +1032,60 @@ extern "C" int bpm_propagate_host(bpm_plan_t p, const void* h_dn, const void* Ei
   return bpm_check(p);
 }
 
+namespace {
+// Single-field plans: time the propagation of slices [0, z_probe) with every
+// transform schedule of the plan's size (one warm-up, one timed call each)
+// and keep the fastest.
+int autotune_schedule(bpm_plan_s* p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
+                      float* const* d_I, int z_probe, cudaStream_t stream) {
+  const int n = p->inst[0].d.nx, count = kSchedules(n);
+  if (count < 2) return BPM_OK;
+  const int keep = p->res.begin()->second.sched;
+  float best = 1e30f;
+  int best_s = keep;
+  cudaEvent_t e0, e1;
+  BPM_CU(cudaEventCreate(&e0));
+  BPM_CU(cudaEventCreate(&e1));
+  const int zp = std::min(z_probe, std::max(1, p->inst[0].d.nz));
+  for (int sc = 0; sc < count; ++sc) {
+    if (switch_schedule(p, sc) != BPM_OK) continue;
+    int rc = bpm_propagate(p, d_dn, d_Ein, d_Eout, d_I, 0, zp, stream);   // warm-up
+    if (rc == BPM_OK) {
+      cudaEventRecord(e0, stream);
+      rc = bpm_propagate(p, d_dn, d_Ein, d_Eout, d_I, 0, zp, stream);
+      cudaEventRecord(e1, stream);
+    }
+    if (rc != BPM_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_s = sc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  const int rc = switch_schedule(p, best_s);
+  if (rc) return rc;
+  return bpm_check(p);
+}
+}  // namespace
+
+extern "C" int bpm_set_schedule(bpm_plan_t p, int schedule) {
+  if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
+  if (p->inst.size() != 1) return fail(BPM_ERR_UNSUPPORTED, "schedules are chosen for single-field plans only");
+  const int n = p->inst[0].d.nx;
+  if (schedule < 0 || schedule >= kSchedules(n))
+    return fail(BPM_ERR_ARG, "size %d has schedules 0..%d, not %d", n, kSchedules(n) - 1, schedule);
+  return switch_schedule(p, schedule);
+}
+
 extern "C" int bpm_autotune(bpm_plan_t p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
                             float* const* d_I, int z_probe, cudaStream_t stream) {
   if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
-  if (p->inst.size() < 2) return BPM_OK;     // single-field plans have one configuration
   if (z_probe < 1) return fail(BPM_ERR_ARG, "z_probe must be >= 1");
+  if (p->inst.size() < 2) return autotune_schedule(p, d_dn, d_Ein, d_Eout, d_I, z_probe, stream);
   const int keep = p->cluster;
   const unsigned keep_flags = p->flags;
   p->flags &= ~(unsigned)BPM_FLAG_GRAPH;

@@ -188,7 +188,10 @@ using Rad6x8x8 = Radices<6, 8, 8>;
 using Rad8x8x4 = Radices<8, 8, 4>;
 using Rad4x8x8 = Radices<4, 8, 8>;
 
-template <int N>
+// Cfg<N, S>: transform schedule S of size N (S = 0 the default; the other
+// schedules of a size are alternatives that bpm_autotune times for
+// single-field plans, kSchedules(N) of them).
+template <int N, int S = 0>
 struct Cfg;
 template <> struct Cfg<64> : LoopCfg<64, 8, 8, 8, 73> {};
 template <> struct Cfg<128> : GroupCfg<128, 8, 145, GroupFFT<128, 8, 8, -1, Rad8x16>, GroupFFT<128, 8, 16, +1, Rad16x8>> {};
@@ -203,6 +206,27 @@ template <> struct Cfg<256> : GroupCfg<256, 32, 274, GroupFFT<256, 32, 16, -1, R
 template <> struct Cfg<384> : GroupCfg<384, 16, 409, GroupFFT<384, 16, 16, -1, Rad8x8x6>, GroupFFT<384, 16, 16, +1, Rad6x8x8>> {};
 template <> struct Cfg<512> : LoopCfg<512, 32, 8, 16, 546> {};
 template <> struct Cfg<1024> : FourStepCfg<LoopCfg<1024, 32, 32, 32, 1058>, 32> {};
+
+// Alternative schedules (single-field plans; bpm_autotune keeps the fastest):
+// 512 as unrolled 8 x 8 x 8 or 16 x 16 x 2 passes with separate inverse
+// schedules, 256 with the pass order reversed or as the rolled radix-16 loop
+// on two rows per warp, 1024 with its columns staged through shared memory
+// like the rows instead of the four-step register layout.
+template <> struct Cfg<512, 1> : GroupCfg<512, 32, 546, GroupFFT<512, 32, 16, -1, Radices<8, 8, 8>>,
+                                          GroupFFT<512, 32, 16, +1, Radices<8, 8, 8>>> {};
+template <> struct Cfg<512, 2> : GroupCfg<512, 32, 546, GroupFFT<512, 32, 16, -1, Radices<16, 16, 2>>,
+                                          GroupFFT<512, 32, 16, +1, Radices<2, 16, 16>>> {};
+template <> struct Cfg<256, 1> : GroupCfg<256, 32, 274, GroupFFT<256, 32, 16, -1, Rad4x8x8>, GroupFFT<256, 32, 16, +1, Rad8x8x4>> {};
+template <> struct Cfg<256, 2> : LoopCfg<256, 16, 16, 16, 273> {};
+template <> struct Cfg<1024, 1> : LoopCfg<1024, 32, 32, 32, 1058> {};
+
+// number of schedules of size n (Cfg<n, 0> .. Cfg<n, kSchedules(n) - 1>)
+__host__ __device__ constexpr int kSchedules(int n) { return n == 256 || n == 512 ? 3 : (n == 1024 ? 2 : 1); }
+// schedule a single-field plan starts with: the fastest measured on a B300
+// (us per slice with the intensity volume: 256^2 6.80 / 6.82 / 8.84,
+// 512^2 10.91 / 10.28 / 9.86, 1024^2 14.15 / 16.14); batched plans always
+// use schedule 0, the one compiled into the batched kernel
+__host__ __device__ constexpr int kDefaultSchedule(int n) { return n == 512 ? 2 : 0; }
 
 // shared memory of the half-step kernels: twiddle tables, then the buffers
 template <class C>
@@ -506,11 +530,11 @@ __device__ __forceinline__ void store_layout(const float2* v, float2* dst, int t
 // Rows [r0, r1) of the team member; each group of T threads takes one row per
 // round.  Groups without a row run the transforms on zeros (so that the warp
 // stays converged for __syncwarp) and skip all memory traffic.
-template <int N, int MODE, bool KAPPA = false, bool PK = true>
+template <int N, int MODE, bool KAPPA = false, bool PK = true, int S = 0>
 __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1, int z, float2* s_buf,
                                               const float2* s_twf, const float2* s_twi, bool& bad,
                                               const Stage& st = Stage()) {
-  using C = Cfg<N>;
+  using C = Cfg<N, S>;
   const int lane = threadIdx.x & 31;
   const int gid = (threadIdx.x >> 5) * C::GPW + lane / C::T;
   const int t = lane % C::T;
@@ -705,10 +729,10 @@ __device__ __forceinline__ void four_step_fwd(float2* v, const float4* tw, float
 // Columns [c0, c1) by four-step transforms (FourStepCfg): load, FFT_y,
 // propagator H^T[col][ky], inverse FFT_y (conjugated forward), store, NG
 // columns per round, all in registers apart from the two exchanges.
-template <int N>
+template <int N, int S = 0>
 __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int c1, int z, float2* s_buf,
                                                  const float2* s_tw4, const Stage& st) {
-  using C = Cfg<N>;
+  using C = Cfg<N, S>;
   constexpr int N1 = C::FS_N1, NG = C::NG, SA = C::FS_SA, SC = C::FS_SC;
   const int c = threadIdx.x % NG, ai = threadIdx.x / NG;
   // [k/2][a][k%2] pairs (16-byte aligned: the table follows whole tables)
@@ -759,13 +783,13 @@ __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int 
 // memory (column g of the round at s_buf + g * GS, index padded like the
 // forward transform's exchange buffer).  Sizes with a four-step layout take
 // col_half_step_4s for the propagator.
-template <int N, int MODE>
+template <int N, int MODE, int S = 0>
 __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1, int z, float2* s_buf,
                                               const float2* s_twf, const float2* s_twi,
                                               const Stage& st = Stage()) {
-  using C = Cfg<N>;
+  using C = Cfg<N, S>;
   if constexpr (C::FS_N1 > 0 && MODE == COL_PROP) {
-    col_half_step_4s<N>(a, c0, c1, z, s_buf, s_twi + C::TWI, st);
+    col_half_step_4s<N, S>(a, c0, c1, z, s_buf, s_twi + C::TWI, st);
     return;
   }
   const int lane = threadIdx.x & 31;
@@ -873,11 +897,11 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
   }
 }
 
-template <int N>
+template <int N, int S = 0>
 __device__ __forceinline__ void load_twiddles(const StepArgs& a, float2* s_twf, float2* s_twi) {
   // the tables are contiguous: forward, inverse, four-step
   (void)s_twi;
-  for (int i = threadIdx.x; i < cfg_twiddles<Cfg<N>>(); i += kThreads) s_twf[i] = __ldg(a.tw + i);
+  for (int i = threadIdx.x; i < cfg_twiddles<Cfg<N, S>>(); i += kThreads) s_twf[i] = __ldg(a.tw + i);
   __syncthreads();
 }
 
@@ -946,9 +970,9 @@ __global__ void bpm_build_gt_kernel(float* gt, int nx, int ny, double dx, double
 // column half-step of slice z starts, so the HBM read overlaps it; the
 // intensity rows are written to shared memory by the row half-step and sent
 // to HBM by one bulk store that overlaps the next column half-step.
-template <int N, bool KAPPA = false>
+template <int N, bool KAPPA = false, int S = 0>
 __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a) {
-  using C = Cfg<N>;
+  using C = Cfg<N, S>;
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
   float2* s_twi = s_twf + C::TWF;
@@ -984,10 +1008,10 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
     for (int i = threadIdx.x; i < (chi - clo) * N; i += kThreads) dst[(i / N) * C::HS + i % N] = __ldg(src + i);
   }
   if (threadIdx.x == 0 && a.dn_stage) mbar_init(&s_mbar, 1);
-  load_twiddles<N>(a, s_twf, s_twi);    // ends with __syncthreads
+  load_twiddles<N, S>(a, s_twf, s_twi);    // ends with __syncthreads
   unsigned epoch = 0, dn_parity = 0;
   bool bad = false, dn_pending = false;
-  row_half_step<N, ROW_FWD>(a, lo, hi, a.z_begin, s_buf, s_twf, s_twi, bad);
+  row_half_step<N, ROW_FWD, false, true, S>(a, lo, hi, a.z_begin, s_buf, s_twf, s_twi, bad);
   if (!team_barrier(a, epoch, &s_flag)) return;
   for (int zi = a.z_begin; zi < a.z_end; ++zi) {
     const bool last = zi + 1 == a.z_end;
@@ -1000,7 +1024,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
       }
       dn_pending = true;
     }
-    col_half_step<N, COL_PROP>(a, clo, chi, z, s_buf, s_twf, s_twi, st);
+    col_half_step<N, COL_PROP, S>(a, clo, chi, z, s_buf, s_twf, s_twi, st);
     if (!team_barrier(a, epoch, &s_flag)) break;
     bool ok = true;
     if (dn_pending) {
@@ -1010,8 +1034,8 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
     }
     if (st.inten && threadIdx.x == 0) bulk_wait_reads();   // previous intensity store has read its rows
     if (__syncthreads_or(!ok)) break;
-    if (!last) row_half_step<N, ROW_STEP, KAPPA>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
-    else row_half_step<N, ROW_LAST, KAPPA>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
+    if (!last) row_half_step<N, ROW_STEP, KAPPA, true, S>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
+    else row_half_step<N, ROW_LAST, KAPPA, true, S>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
     if (st.inten && z >= a.iz0 && z < a.iz1) {
       fence_proxy_async_smem();
       __syncthreads();
@@ -1029,48 +1053,48 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
 }
 
 // One half-step per launch (comparison path and input synthesis).
-template <int N, int MODE, bool KAPPA = false>
+template <int N, int MODE, bool KAPPA = false, int S = 0>
 __global__ void __launch_bounds__(kThreads, 1) bpm_row_kernel(StepArgs a, int z) {
-  using C = Cfg<N>;
+  using C = Cfg<N, S>;
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
   float2* s_twi = s_twf + C::TWF;
   float2* s_buf = s_twi + C::TWI + C::TW4;
-  load_twiddles<N>(a, s_twf, s_twi);
+  load_twiddles<N, S>(a, s_twf, s_twi);
   const int G = gridDim.x, rank = blockIdx.x;
   const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
   bool bad = false;
-  row_half_step<N, MODE, KAPPA>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+  row_half_step<N, MODE, KAPPA, true, S>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
   if constexpr (MODE == ROW_STEP || MODE == ROW_LAST) report_bad(a, bad);
 }
 
-template <int N, int MODE>
+template <int N, int MODE, int S = 0>
 __global__ void __launch_bounds__(kThreads, 1) bpm_col_kernel(StepArgs a, int z) {
-  using C = Cfg<N>;
+  using C = Cfg<N, S>;
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
   float2* s_twi = s_twf + C::TWF;
   float2* s_buf = s_twi + C::TWI + C::TW4;
-  load_twiddles<N>(a, s_twf, s_twi);
+  load_twiddles<N, S>(a, s_twf, s_twi);
   const int G = gridDim.x, rank = blockIdx.x;
   const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
-  col_half_step<N, MODE>(a, lo, hi, z, s_buf, s_twf, s_twi);
+  col_half_step<N, MODE, S>(a, lo, hi, z, s_buf, s_twf, s_twi);
 }
 
 // Light sheet: the ky = 0 spectrum line, inverse FFT_x by group 0 of warp 0,
 // then the row is copied to every y.  Every CTA computes the (short) line
 // itself and writes a share of the rows.  Dynamic shared memory: smem_bytes()
 // plus GS float2 for the spectrum line.
-template <int N>
+template <int N, int S = 0>
 __global__ void __launch_bounds__(kThreads, 1) bpm_light_sheet_kernel(StepArgs a, double w0, double xc) {
-  using C = Cfg<N>;
+  using C = Cfg<N, S>;
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
   float2* s_twi = s_twf + C::TWF;
   float2* s_buf = s_twi + C::TWI + C::TW4;
   float2* line = s_buf + C::BUFLEN;
   __shared__ double s_part[kThreads];
-  load_twiddles<N>(a, s_twf, s_twi);
+  load_twiddles<N, S>(a, s_twf, s_twi);
   const double nd = __dmul_rn((double)N, a.dx);
   // sum of A(kx) over propagating bins (FP64)
   double part = 0.0;

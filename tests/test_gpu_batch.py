@@ -41,7 +41,9 @@ def _run_batch(B, cases, flags=0, tune=False, z=(0, 2 ** 31 - 1)):
         inten = [torch.zeros((max(c[1], 1), c[0], c[0]), dtype=torch.float32, device=dev) for c in cases]
         if tune:
             B.bpm_autotune(plan, dn, ein, eout, inten, 2)
-            assert B.bpm_plan_info(plan)["team_ctas"] in (2, 4, 8, 16)
+            info = B.bpm_plan_info(plan)
+            assert info["team_ctas"] in (2, 4, 8, 16)
+            assert (info["schedule"], info["schedules"]) == (0, 1)     # the batched kernel's own schedules
         B.bpm_propagate(plan, dn, ein, eout, inten, *z)
         assert B.bpm_check(plan) == B.BPM_OK, B.bpm_last_error()
         out1 = [e.cpu().numpy() for e in eout]

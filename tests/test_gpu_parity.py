@@ -224,3 +224,69 @@ def test_argument_errors(B):
         assert ei.value.code == B.BPM_ERR_ARG
     finally:
         B.bpm_free(plan)
+
+
+@pytest.mark.parametrize("n", [256, 512, 1024])
+def test_every_transform_schedule_matches_oracle(B, n):
+    """Every transform schedule of a size (set by bpm_set_schedule; the
+    autotuner picks among them) against the oracle, with index steps that need
+    every phasor form, and the multi-launch path of the same schedule."""
+    nz = 3
+    d = 0.1625 if n == 1024 else 0.1
+    rng = np.random.default_rng(11 * n)
+    dn = np.empty((nz, n, n))
+    dn[0] = rng.uniform(0.0, 0.05, size=(n, n))
+    dn[1] = rng.uniform(0.0, 0.3, size=(n, n))
+    dn[2] = rng.uniform(-1.0, 1.0, size=(n, n))
+    dn[2, ::3] = rng.uniform(0.0, 0.05, size=dn[2, ::3].shape)
+    dn16 = dn.astype(np.float16)
+    E0 = bandlimited_field(n, d, 0.9, n + 5)
+    Er, Ir = oracle.bpm(inputs.dn_to_f64(dn16), E0, d, d, d, 0.5, 1.33)
+    dev = torch.device("cuda")
+    dn_t = torch.from_numpy(dn16).to(dev)
+    e_in = torch.from_numpy(np.ascontiguousarray(E0, np.complex64)).to(dev)
+    for flags in (0, B.BPM_FLAG_MULTI_LAUNCH):
+        plan = B.bpm_plan(B.Instance(n, nz, d, d), flags=flags)
+        try:
+            count = B.bpm_plan_info(plan)["schedules"]
+            assert count >= 2
+            for sc in range(count):
+                B.bpm_set_schedule(plan, sc)
+                assert B.bpm_plan_info(plan)["schedule"] == sc
+                e_out = torch.empty_like(e_in)
+                I = torch.zeros((nz, n, n), dtype=torch.float32, device=dev)
+                B.bpm_propagate(plan, dn_t, e_in, e_out, I)
+                assert B.bpm_check(plan) == B.BPM_OK, B.bpm_last_error()
+                ef = field_rel_l2(e_out.cpu().numpy(), Er)
+                ei = intensity_rel_max(I.cpu().numpy(), Ir)
+                assert ef <= FIELD_TOL / 10, (sc, flags, ef)
+                assert ei <= INTENSITY_TOL / 10, (sc, flags, ei)
+            with pytest.raises(RuntimeError):
+                B.bpm_set_schedule(plan, count)
+        finally:
+            B.bpm_free(plan)
+
+
+def test_autotune_picks_a_schedule_of_a_single_field_plan(B):
+    n, nz, d = 512, 8, 0.1
+    rng = np.random.default_rng(21)
+    dn16 = rng.uniform(0, 0.05, size=(nz, n, n)).astype(np.float16)
+    E0 = bandlimited_field(n, d, 0.9, 77)
+    dev = torch.device("cuda")
+    plan = B.bpm_plan(B.Instance(n, nz, d, d))
+    try:
+        dn_t = torch.from_numpy(dn16).to(dev)
+        e_in = torch.from_numpy(E0).to(dev)
+        e_out = torch.empty_like(e_in)
+        I = torch.zeros((nz, n, n), dtype=torch.float32, device=dev)
+        assert B.bpm_plan_info(plan)["schedule"] == 2          # the size's measured-best start
+        B.bpm_autotune(plan, dn_t, e_in, e_out, I, 4)
+        info = B.bpm_plan_info(plan)
+        assert 0 <= info["schedule"] < info["schedules"] == 3
+        B.bpm_propagate(plan, dn_t, e_in, e_out, I)
+        assert B.bpm_check(plan) == B.BPM_OK, B.bpm_last_error()
+        Er, Ir = oracle.bpm(inputs.dn_to_f64(dn16), E0, d, d, d, 0.5, 1.33)
+        assert field_rel_l2(e_out.cpu().numpy(), Er) <= FIELD_TOL / 10
+        assert intensity_rel_max(I.cpu().numpy(), Ir) <= INTENSITY_TOL / 10
+    finally:
+        B.bpm_free(plan)
