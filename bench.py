@@ -191,6 +191,12 @@ def cpu_baseline(w, dn16, foci, slices: int):
                       f"({dt:.1f} s)"}
 
 
+def workload_name(w, nz: int) -> str:
+    """The headline workload as both arms name it in their config."""
+    return (f"multiplex1024: {w.n}x{w.n}x{nz} voxels, dx=dz={w.d} um, lambda={w.lam} um, "
+            f"n0={w.n0}, 800-sphere FP16 phantom (seed 2), 32x32 foci NA 0.6")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -210,10 +216,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"multiplex1024: {w.n}x{w.n}x{k}-slice sample per step of the 1024^3 "
-                                   f"multiplexed-PSF workload (FP64 CPU oracle)"},
+            "config": {"workload": workload_name(w, dn16.shape[0]), "parallelism": "single host (FP64 CPU oracle)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{k} slices of 1024x1024 per step, with the multiplexed synthesis"},
+                             "sample": f"{k} slices of {w.n}x{w.n} per step of that workload, with the "
+                                       f"multiplexed synthesis"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -398,8 +404,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": value / (PAPER_VOXEL_STEPS_PER_S * ws), "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"multiplex1024: {n}x{n}x{nz} voxels, dx=dz={w.d} um, lambda={w.lam} um, "
-                                   f"n0={w.n0}, 800-sphere FP16 phantom (seed 2), 32x32 foci NA 0.6",
+            "config": {"workload": workload_name(w, nz),
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (2 GiB index volume, 4 GiB intensity volume per step)",
                        "team_ctas": info["team_ctas"], "plan_ms": plan_ms},
