@@ -101,8 +101,10 @@ int bpm_plan(bpm_plan_t *out, const bpm_instance_desc *inst, int n_inst, unsigne
  * field (unless BPM_FLAG_MULTI_LAUNCH).  A plan with several instances (any
  * mix of the supported sizes) runs all of them in one persistent launch of
  * thread-block clusters: each cluster propagates whole instances taken from a
- * device work queue, largest first (with BPM_FLAG_GRAPH the launch and its
- * argument upload are a CUDA graph, captured once per argument set).
+ * device work queue, largest first, while a second launch of two-CTA teams
+ * on the SMs the clusters leave free takes small instances from the other
+ * end of the queue (with BPM_FLAG_GRAPH both launches and the argument upload
+ * are one CUDA graph, captured once per argument set).
  *   d_dn   : host array of n_inst device pointers; instance i reads the FP16
  *            volume [nz_i][ny][nx] (slice z at offset z*nx*ny)
  *   d_Ein  : host array of device pointers to the input fields (entrance of

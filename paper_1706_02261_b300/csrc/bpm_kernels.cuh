@@ -1236,13 +1236,43 @@ struct InstArgs {
 };
 
 struct BatchArgs {
-  const InstArgs* inst;   // [n_inst]
-  const int* order;       // queue order (instance indices, largest first)
+  const InstArgs* inst;         // [n_inst]
+  const int* order;             // queue order (instance indices, largest first)
   int n_inst;
-  unsigned* queue;        // work counter, zeroed before the launch
-  int* slots;             // per-cluster broadcast of the fetched queue position
+  unsigned long long* queue;    // (taken from the front << 32) | taken from the back, zeroed before the launch
+  int* slots;                   // per-cluster broadcast of the fetched queue position
+  int slot_base;                // this launch's first slot (a fill launch follows the main one)
+  int from_back;                // 0: take from the front (largest first); 1: from the back (smallest first)
+  int back_min;                 // a back taker takes no position below this (too large for its team)
   int* err;
 };
+
+// One queue position for a team (its leader thread): the main launch takes
+// positions from the front of the order, a fill launch of smaller teams (on
+// the SMs the main clusters leave free) from the back; one 64-bit word holds
+// both counts, so the two ends never hand out the same position.  Returns
+// n_inst when nothing is left for this taker.  Lock-free: a failed exchange
+// means another team took a position; bounded all the same.
+__device__ __forceinline__ int batch_take(const BatchArgs& b) {
+  for (int tries = 0; tries < (1 << 20); ++tries) {
+    const unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(b.queue);
+    const unsigned front = (unsigned)(cur >> 32), back = (unsigned)cur;
+    if (front + back >= (unsigned)b.n_inst) return b.n_inst;
+    int k;
+    unsigned long long next;
+    if (!b.from_back) {
+      k = (int)front;
+      next = cur + (1ull << 32);
+    } else {
+      k = b.n_inst - 1 - (int)back;
+      if (k < b.back_min) return b.n_inst;
+      next = cur + 1ull;
+    }
+    if (atomicCAS(b.queue, cur, next) == cur) return k;
+  }
+  atomicCAS(b.err, 0, kDevErrTimeout);
+  return b.n_inst;
+}
 
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -1312,9 +1342,9 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_batch_kernel(BatchArgs b) {
   const int CL = (int)cluster_size(), rank = (int)cluster_rank(), cid = (int)cluster_id();
   bool bad = false;
   for (;;) {
-    if (rank == 0 && threadIdx.x == 0) b.slots[cid] = (int)atomicAdd(b.queue, 1u);
+    if (rank == 0 && threadIdx.x == 0) b.slots[b.slot_base + cid] = batch_take(b);
     cluster_sync_all();
-    const int k = ld_volatile(b.slots + cid);
+    const int k = ld_volatile(b.slots + b.slot_base + cid);
     cluster_sync_all();     // every CTA has read the slot before the leader may overwrite it
     if (k >= b.n_inst) break;
     const InstArgs ia = b.inst[b.order[k]];
