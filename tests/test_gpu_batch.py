@@ -145,3 +145,34 @@ def test_batch_every_phasor_form(B):
         Er, Ir = oracle.bpm(inputs.dn_to_f64(dn16), E0, d, d, d, 0.5, 1.33)
         assert field_rel_l2(Eg, Er) <= FIELD_TOL / 10, n
         assert intensity_rel_max(Ig, Ir) <= INTENSITY_TOL / 10, n
+
+
+def test_batch_every_instance_exactly_once_with_fill_teams(B):
+    """Many small instances behind two large ones: the main cluster teams take
+    positions from the large end of the queue while the fill launch's two-CTA
+    teams take small ones from the other end.  Every output must be its own
+    instance's propagation (an instance taken twice or never would leave a
+    wrong or untouched output; outputs start as NaN)."""
+    cases = []
+    for k in range(2):
+        rng = np.random.default_rng(500 + k)
+        cases.append((512, 8, 0.1, rng.uniform(0, 0.05, size=(8, 512, 512)).astype(np.float16),
+                      bandlimited_field(512, 0.1, 0.85, 600 + k)))
+    for k in range(40):
+        rng = np.random.default_rng(700 + k)
+        cases.append((64, 3, 0.1, rng.uniform(0, 0.05, size=(3, 64, 64)).astype(np.float16),
+                      bandlimited_field(64, 0.1, 0.85, 800 + k)))
+    dev = torch.device("cuda")
+    plan = B.bpm_plan([B.Instance(n, nz, d, d) for (n, nz, d, _, _) in cases], flags=B.BPM_FLAG_GRAPH)
+    try:
+        dn = [torch.from_numpy(c[3]).to(dev) for c in cases]
+        ein = [torch.from_numpy(c[4]).to(dev) for c in cases]
+        for rep in range(2):
+            eout = [torch.full_like(e, float("nan")) for e in ein]
+            B.bpm_propagate(plan, dn, ein, eout, None)
+            assert B.bpm_check(plan) == B.BPM_OK, B.bpm_last_error()
+            for (n, nz, d, dn16, E0), eg in zip(cases, eout):
+                Er, _ = oracle.bpm(inputs.dn_to_f64(dn16), E0, d, d, d, 0.5, 1.33, want_intensity=False)
+                assert field_rel_l2(eg.cpu().numpy(), Er) <= FIELD_TOL / 10, (n, rep)
+    finally:
+        B.bpm_free(plan)
