@@ -498,11 +498,11 @@ int enqueue_batch(bpm_plan_s* p, int clusters, cudaStream_t s) {
   BPM_CU(cudaMemcpyAsync(p->d_inst, p->h_inst, sizeof(InstArgs) * n, cudaMemcpyHostToDevice, s));
   BPM_CU(cudaMemsetAsync(p->d_queue, 0, sizeof(unsigned long long), s));
   // fill teams: positions in the order (largest first) whose cost on a fill
-  // team is at most a quarter of the first one's on a main team, which bounds
-  // the tail a fill team can add after the queue runs dry (at one half and
-  // more the fill teams became the tail: batch64 33.1 -> 41.2 ms; at a
-  // quarter 31.8 ms)
-  constexpr int kFillCluster = 2, kFillTail = 4;
+  // team is at most a third of the first one's on a main team, which bounds
+  // the tail a fill team can add after the queue runs dry (batch64: 41.2 ms
+  // at one half, where the fill teams became the tail; 31.5 ms at a third,
+  // 32.0 ms at a quarter, 33.0 ms at a sixth)
+  constexpr int kFillCluster = 2, kFillTail = 3;
   const int fill = p->cluster > kFillCluster ? (p->sms - clusters * p->cluster) / kFillCluster : 0;
   int back_min = n;
   if (fill > 0) {
