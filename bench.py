@@ -182,19 +182,37 @@ def make_workload(nz: int):
     return w, dn, w.foci()
 
 
-def cpu_baseline(w, dn16, foci, slices: int):
+def cpu_baseline(w, dn16, foci, slices: int, want_output: bool = False):
     """The FP64 oracle, as it stands, on the first ``slices`` slices of the
-    same workload (synthesis of the same multiplexed field + propagation)."""
+    same workload (synthesis of the same multiplexed field + propagation).
+    With ``want_output`` also returns the oracle's field after the sample and
+    its intensity planes, for the parity figures of the bench line."""
     import oracle
     from paper_1706_02261_b300 import inputs
     dn64 = inputs.dn_to_f64(dn16[:slices])
     t0 = time.perf_counter()
     E0 = oracle.multiplex_psf(w.n, w.n, w.d, w.d, w.lam, w.n0, foci.ix, foci.iy, foci.phase, foci.zf, foci.NA)
-    oracle.bpm(dn64, E0, w.d, w.d, w.d, w.lam, w.n0)
+    Er, Ir = oracle.bpm(dn64, E0, w.d, w.d, w.d, w.lam, w.n0)
     dt = time.perf_counter() - t0
-    return {"value": w.n * w.n * slices / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{w.n}x{w.n}x{slices} slices of the 1024^3 workload incl. the multiplexed synthesis "
-                      f"({dt:.1f} s)"}
+    res = {"value": w.n * w.n * slices / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{w.n}x{w.n}x{slices} slices of the 1024^3 workload incl. the multiplexed synthesis "
+                     f"({dt:.1f} s)"}
+    return (res, Er, Ir) if want_output else res
+
+
+def parity_figures(Eg, Ig, Er, Ir, slices: int):
+    """Error of the GPU's results against the FP64 oracle on the same inputs:
+    field relative L2 after the sample's last slice, and the peak-normalised
+    maximum intensity error over the sample's planes."""
+    Eg = np.asarray(Eg, np.complex128)
+    field = float(np.linalg.norm(Eg - Er) / np.linalg.norm(Er))
+    num, peak = 0.0, 0.0
+    for z in range(slices):
+        num = max(num, float(np.max(np.abs(np.asarray(Ig[z], np.float64) - Ir[z]))))
+        peak = max(peak, float(np.max(Ir[z])))
+    return {"slices": slices, "field_rel_l2": field, "intensity_rel_max": num / peak,
+            "gates": {"field_rel_l2": 1e-4, "intensity_rel_max": 1e-3},
+            "reference": "FP64 CPU oracle (oracle/bpm_oracle.c) on the same FP16 index values and emitter list"}
 
 
 def workload_name(w, nz: int) -> str:
@@ -402,8 +420,18 @@ def run_ours(args):
         cufft = cufft_slice_loop(w, dn_d, e0, eout, stream)
 
     cpu = None
+    parity = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(w, dn16, foci, args.cpu_slices)
+        ks = min(args.cpu_slices, nz)
+        cpu, Er, Ir = cpu_baseline(w, dn16, foci, ks, want_output=True)
+        # the same sample on the GPU: the timed steps' intensity planes
+        # [0, ks) and the field after slice ks (one more call, untimed)
+        ek = torch.empty_like(e0)
+        B.bpm_propagate(plan, dn_d, e0, ek, None, 0, ks, stream)
+        if B.bpm_check(plan) != 0:
+            raise SystemExit(f"device error in the parity call: {B.bpm_last_error()}")
+        parity = parity_figures(ek.cpu().numpy(), inten[:ks].cpu().numpy(), Er, Ir, ks)
+        del Er, Ir
 
     launches_per_step = 6     # pupil count, scatter, 3 synthesis half-steps, persistent propagation (device leg)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -415,7 +443,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (2 GiB index volume, 4 GiB intensity volume per step)",
                        "team_ctas": info["team_ctas"], "plan_ms": plan_ms},
             "roofline": roofline, "clocks": clocks.summary(), "gpu_launches": launches_per_step * args.steps,
-            "e2e": e2e, "cpu_baseline": cpu, "cufft_comparison": cufft}
+            "e2e": e2e, "cpu_baseline": cpu, "parity": parity, "cufft_comparison": cufft}
     if rank == 0:
         print(json.dumps(line), flush=True)
     B.bpm_free(plan)

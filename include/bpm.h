@@ -199,8 +199,11 @@ int bpm_demultiplex(bpm_plan_t p, int inst, const float *d_I, int w_begin, int w
  *   d_dn, d_Ein, d_Eout, d_I, z_begin, z_end : as for bpm_propagate, for this
  *                   one instance (d_I may be NULL)
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call rebuilds the tables and clears the counter
+ * (cudaGetSymbolAddress) with that device current and keeps it for the rest of
+ * the process; make that first call before any stream capture.  The kept
+ * address belongs to the device's current context: after cudaDeviceReset on
+ * that device it is stale, so do not call this function again on a device
+ * that has been reset.  Every call rebuilds the tables and clears the counter
  * and error word on `stream`, runs the propagation, then synchronises `stream`
  * and returns the device status (BPM_ERR_TIMEOUT, BPM_ERR_NAN) directly.  All
  * calls on a device share the array, so calls that overlap on the GPU (other

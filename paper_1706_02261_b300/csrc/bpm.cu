@@ -57,6 +57,15 @@ bool supported_n(int n) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Position of the twiddle of butterfly b, radix element r, thread t within
+// one pass's table of a transform with T threads: [b][r][t], or with `paired`
+// (LoopFFT, even R) [b][r/2][t][r%2] so that a thread reads the twiddles of
+// r and r + 1 with one 16-byte load.  Host and device table builders both use
+// it, so their layouts cannot drift apart.
+__host__ __device__ inline size_t twiddle_slot(int b, int r, int t, int R, int T, bool paired) {
+  return paired ? ((size_t)(b * (R / 2) + r / 2) * T + t) * 2 + (r & 1) : (size_t)(b * R + r) * T + t;
+}
+
 // Host-built twiddle table of one transform (FP64, rounded once): for every
 // pass p >= 1 of the radix list, N entries holding W_{Ns R}^{(j mod Ns) r},
 // j = t + b T, with the transform's sign, laid out [b][r][t], or with
@@ -77,9 +86,7 @@ void append_twiddles(std::vector<float2>& out, int N, int T, const std::vector<i
             const int j = t + b * T;
             const long long e = (long long)(j % Ns) * r % (long long)(Ns * R);
             const double ang = sign * kTwoPi * (double)e / (double)(Ns * R);
-            const size_t at = paired ? ((size_t)(b * (R / 2) + r / 2) * T + t) * 2 + (r & 1)
-                                     : (size_t)(b * R + r) * T + t;
-            out[base + at] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            out[base + twiddle_slot(b, r, t, R, T, paired)] = make_float2((float)std::cos(ang), (float)std::sin(ang));
           }
     }
     Ns *= R;
@@ -1208,14 +1215,18 @@ constexpr int kStaticMaxDevices = 64;
 std::mutex g_static_mutex;
 unsigned char* g_static_ptr[kStaticMaxDevices] = {};
 
-// Radix schedule of one transform, passed by value to the twiddle kernel.
+// Radix schedule of one transform, passed by value to the twiddle kernel;
+// `paired` selects the layout the rolled-loop transforms read (LoopFFT: the
+// twiddles of r and r + 1 side by side).
 struct TwSchedule {
-  int n, t, count, sign;
+  int n, t, count, sign, paired;
   int r[4];
 };
 
-// Same table as append_twiddles(), built on the device in FP64: entry
-// (b R + r) T + t of pass p >= 1 holds W_{Ns R}^{(j mod Ns) r}, j = t + b T.
+// Same table as append_twiddles(), built on the device in FP64: for pass
+// p >= 1 the twiddle W_{Ns R}^{(j mod Ns) r}, j = t + b T, of (b, r, t) goes
+// to entry (b R + r) T + t, or with `paired` to ((b R/2 + r/2) T + t) 2 + r%2
+// (twiddle_slot(), shared with the host builder).
 __global__ void bpm_static_twiddle_kernel(float2* out, TwSchedule s) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (s.count - 1) * s.n) return;
@@ -1230,7 +1241,7 @@ __global__ void bpm_static_twiddle_kernel(float2* out, TwSchedule s) {
   const double ang = s.sign * 6.283185307179586 * (double)ex / (double)(Ns * R);
   double sn, cs;
   sincos(ang, &sn, &cs);
-  out[e] = make_float2((float)cs, (float)sn);
+  out[(size_t)(p - 1) * s.n + twiddle_slot(b, r, t, R, s.t, s.paired != 0)] = make_float2((float)cs, (float)sn);
 }
 
 template <class RS>
@@ -1292,6 +1303,7 @@ int static_propagate(const bpm_instance_desc& d, unsigned char* scratch, const v
     s.t = C::T;
     s.count = C::E::NP;
     s.sign = -1;
+    s.paired = 1;
     for (int i = 0; i < C::E::NP && i < 4; ++i) s.r[i] = C::E::R;
     rc = launch_static_twiddles(s, tw, stream);
   } else {

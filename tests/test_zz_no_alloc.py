@@ -4,9 +4,10 @@ bpm_propagate_static serves callers that cannot allocate device memory (a
 host application whose allocator owns the device, a loop that cannot afford
 cudaMalloc's synchronisation, code that must not fail on memory after
 start-up).  It keeps its tables in one fixed device array inside the library,
-shared by every call, so this test makes two calls in a row with different
-grids and spacings and checks that each matches the plan-based entry point
-within the parity tolerances.  The file is named to be collected last.
+shared by every call, so this test makes calls in a row with different
+grids and spacings (every grid it accepts) and checks that each matches the
+plan-based entry point within the parity tolerances; one more call is checked
+against the FP64 oracle directly.  The file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -14,6 +15,8 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+import oracle  # noqa: E402
+from paper_1706_02261_b300 import inputs  # noqa: E402
 from tests.gpu_util import FIELD_TOL, INTENSITY_TOL, bandlimited_field, field_rel_l2, intensity_rel_max  # noqa: E402
 
 
@@ -45,7 +48,12 @@ def _with_plan(B, inst, dn, e0):
 
 def test_static_entry_point_matches_plan_path_twice(B):
     dev = torch.device("cuda")
-    cases = [(B.Instance(256, 6, 0.1, 0.1), 21), (B.Instance(192, 5, 0.12, 0.15), 22)]
+    # every grid the entry point accepts (the rolled-loop 64, the unrolled 128,
+    # 192 and 256 transforms, whose twiddle tables differ in layout), called
+    # back to back with different grids and spacings on the one shared array
+    cases = [(B.Instance(256, 6, 0.1, 0.1), 21), (B.Instance(192, 5, 0.12, 0.15), 22),
+             (B.Instance(64, 7, 0.1, 0.1), 23), (B.Instance(128, 4, 0.11, 0.1), 24),
+             (B.Instance(64, 3, 0.09, 0.12), 25)]
     for inst, seed in cases:
         dn16, E0 = _case(inst.n, inst.nz, inst.dx, seed)
         dn = torch.from_numpy(dn16).to(dev)
@@ -57,6 +65,21 @@ def test_static_entry_point_matches_plan_path_twice(B):
         Ep, Ip = _with_plan(B, inst, dn, e0)
         assert field_rel_l2(Es, Ep) <= FIELD_TOL
         assert intensity_rel_max(Is, Ip) <= INTENSITY_TOL
+
+
+def test_static_entry_point_matches_oracle(B):
+    """One call checked against the FP64 oracle directly (not only through
+    the plan path), on the rolled-loop size."""
+    dev = torch.device("cuda")
+    inst = B.Instance(64, 12, 0.1, 0.1)
+    dn16, E0 = _case(inst.n, inst.nz, inst.dx, 31)
+    e0 = torch.from_numpy(E0).to(dev)
+    out = torch.empty_like(e0)
+    inten = torch.zeros((inst.nz, inst.n, inst.n), dtype=torch.float32, device=dev)
+    assert B.bpm_propagate_static(inst, torch.from_numpy(dn16).to(dev), e0, out, inten) == B.BPM_OK
+    Er, Ir = oracle.bpm(inputs.dn_to_f64(dn16), E0, inst.dx, inst.dx, inst.dz, inst.lam, inst.n0)
+    assert field_rel_l2(out.cpu().numpy(), Er) <= FIELD_TOL
+    assert intensity_rel_max(inten.cpu().numpy(), Ir) <= INTENSITY_TOL
 
 
 def test_static_entry_point_rejects_large_grids(B):
