@@ -66,10 +66,14 @@ enum {
 
 typedef struct bpm_plan_s *bpm_plan_t;
 
-/* One propagation problem (one field).  Grid sizes nx = ny must be one of
- * 64, 128, 192, 256, 384, 512, 1024 (products of 2 and 3 the FFT kernels are
- * built for); nz >= 0.  dx, dy, dz, lambda and n0 must be positive.  tilt_x,
- * tilt_y are unused by the propagation and reserved for input helpers. */
+/* One propagation problem (one field): rows of nx points along x, ny rows
+ * along y, nz slices.  nx and ny must each be one of 64, 96, 128, 192, 256,
+ * 384, 512, 768, 1024, 1536, 2048 (the products of 2 and 3 the FFT kernels are
+ * built for) with nx * ny <= 2^22, e.g. the 1024 x 2048 lateral grid of the
+ * paper's 10^6-PSF calculation (light-sheet paragraph); nz >= 0.  Batched
+ * plans (several instances) take square grids of 64, 128, 192, 256, 384, 512
+ * or 1024.  dx, dy, dz, lambda and n0 must be positive.  tilt_x, tilt_y are
+ * unused by the propagation and reserved for input helpers. */
 typedef struct {
     int nx, ny, nz;
     double dx, dy, dz, lambda, n0;
@@ -98,7 +102,9 @@ int bpm_plan(bpm_plan_t *out, const bpm_instance_desc *inst, int n_inst, unsigne
  * forward 2D DFT, the propagator multiply, the inverse 2D DFT, the phase screen
  * exp(i k0 dn dz) and the intensity |E|^2.  A single-instance plan runs the
  * whole loop in one cooperative persistent launch in which all SMs share the
- * field (unless BPM_FLAG_MULTI_LAUNCH).  A plan with several instances (any
+ * field, for square grids and grids whose sides differ by a factor of two;
+ * other grids (and BPM_FLAG_MULTI_LAUNCH) take one launch per half-step
+ * (bpm_plan_info reports which).  A plan with several instances (any
  * mix of the supported sizes) runs all of them in one persistent launch of
  * thread-block clusters: each cluster propagates whole instances taken from a
  * device work queue, largest first, while a second launch of two-CTA teams
@@ -174,9 +180,9 @@ int bpm_phase_conjugate(bpm_plan_t p, int inst, void *d_E, cudaStream_t stream);
  * for k < pz, y < py, x < px, with lateral indices taken modulo the grid size
  * (the periodic boundary of the propagation) and 0 for slices outside the
  * window [w_begin, w_begin + w_nz).
- *   inst     : instance whose grid (nx = ny) is used
+ *   inst     : instance whose grid (nx, ny) is used
  *   d_I      : device float window [w_nz][ny][nx] (slice z at (z - w_begin)*nx*ny)
- *   h_foci   : host array of n_foci (ix, iy, iz) voxel triples, 0 <= ix, iy < nx
+ *   h_foci   : host array of n_foci (ix, iy, iz) voxel triples, 0 <= ix < nx, 0 <= iy < ny
  *   d_out    : device float [n_foci][pz][py][px], written with streaming stores
  * Errors: BPM_ERR_ARG (focus outside the grid, bad sizes, NULL), BPM_ERR_CUDA. */
 int bpm_demultiplex(bpm_plan_t p, int inst, const float *d_I, int w_begin, int w_nz, int n_foci,
@@ -193,9 +199,10 @@ int bpm_demultiplex(bpm_plan_t p, int inst, const float *d_I, int w_begin, int w
  * the library (about 528 KiB), which every GPU that loads the library keeps
  * until the process exits.  The paper has no counterpart; it is a service of
  * this library.
- *   inst          : one problem description; nx = ny must be 64, 128, 192 or
- *                   256 (larger grids return BPM_ERR_UNSUPPORTED: the fixed
- *                   array holds the propagator of a 256 x 256 grid at most)
+ *   inst          : one problem description; nx = ny must be 64, 96, 128,
+ *                   192 or 256 (larger or rectangular grids return
+ *                   BPM_ERR_UNSUPPORTED: the fixed array holds the propagator
+ *                   of a 256 x 256 grid at most)
  *   d_dn, d_Ein, d_Eout, d_I, z_begin, z_end : as for bpm_propagate, for this
  *                   one instance (d_I may be NULL)
  * The first call on a device looks up the array's device address
@@ -296,16 +303,17 @@ int bpm_plan_info(bpm_plan_t p, int *out, int n_out);
  * buffers and keep the fastest configuration for later calls.  Batched plans:
  * every instance with each cluster size (2, 4, 8, 16 CTAs per team).
  * Single-field plans: each transform schedule of the grid size (radix order
- * and pass structure of the row and column transforms: 256 and 512 have three,
- * 1024 two, the other sizes one).  Overwrites d_Eout and the first z_probe
+ * and pass structure of the row and column transforms: square grids of 256
+ * and 512 have three, 1024 two, the other grids one).  Overwrites d_Eout and the first z_probe
  * intensity slices; synchronises the stream (and the device when the
  * schedule changes).  Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
 int bpm_autotune(bpm_plan_t p, const void *const *d_dn, const void *const *d_Ein, void *const *d_Eout,
                  float *const *d_I, int z_probe, cudaStream_t stream);
 
 /* bpm_set_schedule - single-field plans: use transform schedule `schedule`
- * (0 .. out[6] - 1 of bpm_plan_info; a plan starts with the schedule measured
- * fastest for its size, 2 for 512 and 0 for the others).
+ * (0 .. out[6] - 1 of bpm_plan_info; a square plan starts with the schedule
+ * measured fastest for its size, 2 for 512 and 0 for the others; the rows and
+ * columns of a rectangular grid each take their length's).
  * Results of every schedule agree to FP32 rounding.  Synchronises the device
  * when the schedule changes.  Errors: BPM_ERR_ARG (NULL plan, schedule out of
  * range), BPM_ERR_UNSUPPORTED (batched plan), BPM_ERR_CUDA. */

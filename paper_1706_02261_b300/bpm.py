@@ -32,7 +32,10 @@ BPM_FLAG_MULTI_LAUNCH = 0x2
 BPM_FLAG_GRAPH = 0x4
 BPM_FLAG_ADAPTIVE = 0x8
 
-SUPPORTED_N = (64, 128, 192, 256, 384, 512, 1024)
+# transform lengths of each grid side (nx, ny in this set, nx ny <= 2^22);
+# batched plans take square grids of BATCH_N
+SUPPORTED_N = (64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048)
+BATCH_N = (64, 128, 192, 256, 384, 512, 1024)
 
 
 class BpmError(RuntimeError):
@@ -121,7 +124,8 @@ def _arr(ptrs):
 
 @dataclass
 class Instance:
-    """One propagation problem (grid, spacings in um, vacuum wavelength, n0)."""
+    """One propagation problem: grid n x ny (n = nx, the row length; ny
+    defaults to n) x nz, spacings in um, vacuum wavelength, n0."""
     n: int
     nz: int
     dx: float
@@ -129,9 +133,18 @@ class Instance:
     lam: float = 0.5
     n0: float = 1.33
     dy: float | None = None
+    ny: int | None = None
+
+    @property
+    def nx(self) -> int:
+        return self.n
+
+    @property
+    def rows(self) -> int:
+        return self.ny or self.n
 
     def desc(self) -> bpm_instance_desc:
-        return bpm_instance_desc(self.n, self.n, self.nz, self.dx, self.dy or self.dx, self.dz,
+        return bpm_instance_desc(self.n, self.rows, self.nz, self.dx, self.dy or self.dx, self.dz,
                                  self.lam, self.n0, 0.0, 0.0)
 
 
@@ -198,7 +211,7 @@ def bpm_phase_conjugate(plan, inst: int, e, stream=None) -> int:
 
 def bpm_demultiplex(plan, inst: int, inten, w_begin: int, foci, patch, out, stream=None) -> int:
     """Cut patch = (px, py, pz) around each focus (rows of foci: ix, iy, iz
-    voxel indices) out of the intensity window inten [w_nz][n][n] that starts
+    voxel indices) out of the intensity window inten [w_nz][ny][nx] that starts
     at slice w_begin; out: float tensor [n_foci][pz][py][px]."""
     f = np.ascontiguousarray(np.asarray(foci, dtype=np.int32).reshape(-1, 3))
     px, py, pz = patch
@@ -286,7 +299,7 @@ def bpm_debug_set_barrier_timeout(plan, timeout_ns: int, extra_arrivals: int = 0
 
 def bpm_propagate_static(instance: "Instance", dn, e_in, e_out, inten=None, z_begin: int = 0,
                          z_end: int = 2 ** 31 - 1, stream=None) -> int:
-    """Allocation-free propagation of one instance (grids up to 256 x 256);
+    """Allocation-free propagation of one instance (square grids up to 256 x 256);
     synchronises the stream and returns the device status."""
     desc = instance.desc()
     return _check(_lib.bpm_propagate_static(ctypes.byref(desc), _ptr(dn), _ptr(e_in), _ptr(e_out),

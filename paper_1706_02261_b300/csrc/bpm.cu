@@ -2,10 +2,12 @@
 //
 // Plans validate problem descriptions, build the FP64 propagator tables and the
 // FFT twiddle tables on the device, and pick the team (number of CTAs that
-// share one field).  Propagation is one cooperative persistent launch per
-// instance: the team loops over all slices with two device-wide barriers per
-// slice (see bpm_kernels.cuh).  Every entry point returns a status code and
-// records a message for bpm_last_error().
+// share one field).  Propagation of a single field is one cooperative
+// persistent launch: the team loops over all slices with two device-wide
+// barriers per slice (see bpm_kernels.cuh); grids without a persistent kernel
+// run one launch per half-step.  The kernels themselves are compiled in the
+// ops_*.cu units and found through the registry of bpm_ops.h.  Every entry
+// point returns a status code and records a message for bpm_last_error().
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,12 +20,55 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "bpm.h"
-#include "bpm_kernels.cuh"
+#include "bpm_aux_kernels.cuh"
+#include "bpm_ops.h"
 
 using namespace bpmk;
+
+namespace bpmk {
+
+static OpsRegistry& registry() {
+  static OpsRegistry r;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    register_ops_small(r);
+    register_ops_256(r);
+    register_ops_384(r);
+    register_ops_512(r);
+    register_ops_1024(r);
+    register_ops_2048(r);
+  });
+  return r;
+}
+
+const LenOps* find_len_ops(int n, int sched) {
+  for (const LenOps& o : registry().lens)
+    if (o.n == n && o.sched == sched) return &o;
+  return nullptr;
+}
+
+const PairOps* find_pair_ops(int nx, int ny, int sched) {
+  for (const PairOps& o : registry().pairs)
+    if (o.nx == nx && o.ny == ny && o.sched == sched) return &o;
+  return nullptr;
+}
+
+const std::vector<int>& supported_lengths() {
+  static std::vector<int> v = [] {
+    std::vector<int> r;
+    for (const LenOps& o : registry().lens)
+      if (std::find(r.begin(), r.end(), o.n) == r.end()) r.push_back(o.n);
+    std::sort(r.begin(), r.end());
+    return r;
+  }();
+  return v;
+}
+
+}  // namespace bpmk
 
 namespace {
 
@@ -47,95 +92,45 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 constexpr double kTwoPi = 6.283185307179586;
+constexpr long long kMaxPixels = 1ll << 22;   // nx ny at most (a 2048 x 2048 slice)
 
-bool supported_n(int n) {
-  switch (n) {
-    case 64: case 128: case 192: case 256: case 384: case 512: case 1024: return true;
-    default: return false;
+bool supported_len(int n) {
+  const std::vector<int>& v = supported_lengths();
+  return std::find(v.begin(), v.end(), n) != v.end();
+}
+
+int default_schedule(int n) {
+  for (int s = 0;; ++s) {
+    const LenOps* o = find_len_ops(n, s);
+    if (!o) return 0;
+    if (o->is_default) return s;
   }
+}
+
+int schedule_count(int n) {
+  const LenOps* o = find_len_ops(n, 0);
+  return o ? o->schedules : 0;
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Position of the twiddle of butterfly b, radix element r, thread t within
-// one pass's table of a transform with T threads: [b][r][t], or with `paired`
-// (LoopFFT, even R) [b][r/2][t][r%2] so that a thread reads the twiddles of
-// r and r + 1 with one 16-byte load.  Host and device table builders both use
-// it, so their layouts cannot drift apart.
-__host__ __device__ inline size_t twiddle_slot(int b, int r, int t, int R, int T, bool paired) {
-  return paired ? ((size_t)(b * (R / 2) + r / 2) * T + t) * 2 + (r & 1) : (size_t)(b * R + r) * T + t;
-}
-
-// Host-built twiddle table of one transform (FP64, rounded once): for every
-// pass p >= 1 of the radix list, N entries holding W_{Ns R}^{(j mod Ns) r},
-// j = t + b T, with the transform's sign, laid out [b][r][t], or with
-// `paired` (LoopFFT, even R) [b][r/2][t][r%2] so that a thread reads the
-// twiddles of r and r + 1 with one 16-byte load.
-void append_twiddles(std::vector<float2>& out, int N, int T, const std::vector<int>& radices, int sign,
-                     bool paired = false) {
-  int Ns = 1;
-  for (size_t p = 0; p < radices.size(); ++p) {
-    const int R = radices[p];
-    if (p > 0) {
-      const int B = N / (R * T);
-      const size_t base = out.size();
-      out.resize(base + (size_t)N);
-      for (int b = 0; b < B; ++b)
-        for (int r = 0; r < R; ++r)
-          for (int t = 0; t < T; ++t) {
-            const int j = t + b * T;
-            const long long e = (long long)(j % Ns) * r % (long long)(Ns * R);
-            const double ang = sign * kTwoPi * (double)e / (double)(Ns * R);
-            out[base + twiddle_slot(b, r, t, R, T, paired)] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-          }
-    }
-    Ns *= R;
-  }
-}
-
-template <class RS>
-std::vector<int> radix_list() {
-  std::vector<int> r;
-  for (int i = 0; i < RS::count; ++i) r.push_back(RS::at(i));
-  return r;
-}
-
-template <int N, int S = 0>
-std::vector<float2> twiddles_for() {
-  using C = Cfg<N, S>;
-  std::vector<float2> v;
-  if constexpr (C::kLoop) {
-    append_twiddles(v, N, C::T, std::vector<int>(C::E::NP, C::E::R), -1, true);
-  } else {
-    append_twiddles(v, N, C::T, radix_list<typename C::F::Rad>(), -1);
-    append_twiddles(v, N, C::T, radix_list<typename C::I::Rad>(), +1);
-  }
-  if constexpr (C::TW4 > 0) {
-    // four-step column transform: W_N^(a k), forward sign, laid out
-    // [k/2][a][k%2] (the twiddles of k and k + 1 in one 16-byte load)
-    const int N1 = C::FS_N1;
-    for (int kp = 0; kp < N1 / 2; ++kp)
-      for (int a = 0; a < N1; ++a)
-        for (int k = 2 * kp; k < 2 * kp + 2; ++k) {
-          const long long e = (long long)a * k % N;
-          const double ang = -kTwoPi * (double)e / (double)N;
-          v.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
-        }
-  }
-  return v;
-}
-
 }  // namespace
 
-struct NRes {
-  int n = 0;
+// One transform length (and schedule) used by a plan: its kernels and its
+// twiddle table on the device.
+struct LenRes {
+  const LenOps* ops = nullptr;
   float2* tw = nullptr;
-  float2* tmp = nullptr;    // N x N scratch for input synthesis (allocated on first use)
-  int sched = 0;            // transform schedule (Cfg<n, sched>)
-  int team = 0;             // CTAs per field
-  size_t smem = 0;          // dynamic shared memory of the half-step kernels
-  size_t smem_persist = 0;  // ... of the persistent kernel (with its staging buffers)
-  int rmax = 0;             // rows (= columns) per team CTA at most
+};
+
+// The persistent launch of a single-field plan (ops == nullptr: the grid has
+// no persistent kernel and runs one launch per half-step).
+struct GridRes {
+  const PairOps* ops = nullptr;
+  float2* tw = nullptr;           // combined row + column table (owned)
+  int team = 0;                   // CTAs per field
+  size_t smem_persist = 0;        // dynamic shared memory with the staging buffers
+  int rmax_r = 0, rmax_c = 0;     // rows / columns per team CTA at most
   int h_res = 0, dn_stage = 0, i_stage = 0;
 };
 
@@ -148,9 +143,13 @@ struct InstPlan {
 
 struct bpm_plan_s {
   std::vector<InstPlan> inst;
-  std::map<int, NRes> res;
+  std::map<std::pair<int, int>, LenRes> lens;   // (length, schedule) -> kernels and table
+  std::map<std::pair<int, int>, float2*> tmp;   // (nx, ny) -> field scratch of the input synthesis
+  GridRes grid;                     // single-field plans
+  int sched = 0;                    // schedule of a single-field square plan
   unsigned flags = 0;
   int dev = 0, sms = 0;
+  size_t max_optin = 0;
   unsigned* bar = nullptr;
   int* err = nullptr;
   unsigned long long* npupil = nullptr;
@@ -188,84 +187,122 @@ struct bpm_plan_s {
 
 namespace {
 
-template <int N, int S>
-int setup_kernels(NRes& r, int sms) {
-  using C = Cfg<N, S>;
-  r.smem = cfg_smem_bytes<C>();
-  const int smem = (int)r.smem;
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_FWD, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_STEP, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_LAST, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_STEP, true, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_LAST, true, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_row_kernel<N, ROW_INV_ACC, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_col_kernel<N, COL_PROP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_col_kernel<N, COL_FOCUS, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_light_sheet_kernel<N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem + (int)(C::GS * sizeof(float2))));
-  // smallest team that gives every group one row per half-step, at most one
-  // CTA per SM; with the four-step column layout every SM takes rows (fewer
-  // rows per CTA) while the columns stay in aligned groups of NG
-  const int want = C::FS_N1 > 0 ? N : (N + C::NG - 1) / C::NG;
-  r.team = std::max(1, std::min(want, sms));
-  // staging buffers of the persistent kernel, dropped (propagator columns
-  // first) if they would not fit next to the group buffers
-  int max_optin = 0;
-  BPM_CU(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, 0));
-  // rows (and columns) per CTA at most: columns come in whole groups of NG
-  r.rmax = (N + r.team - 1) / r.team;
-  r.rmax = (r.rmax + C::NG - 1) / C::NG * C::NG;
-  auto rup = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  const size_t hb = rup((size_t)r.rmax * C::HS * sizeof(float2)), db = rup((size_t)r.rmax * N * 2),
-               ib = rup((size_t)r.rmax * N * sizeof(float));
-  const size_t budget = (size_t)max_optin - 1024;   // static shared memory of the kernel
-  r.h_res = r.dn_stage = r.i_stage = 1;
-  if (r.smem + hb + db + ib > budget) r.h_res = 0;
-  if (r.smem + db + ib > budget) r.i_stage = 0;
-  if (r.smem + db > budget) r.dn_stage = 0;
-  r.smem_persist = r.smem + (r.h_res ? hb : 0) + (r.dn_stage ? db : 0) + (r.i_stage ? ib : 0);
-  BPM_CU(cudaFuncSetAttribute(bpm_persistent_kernel<N, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)r.smem_persist));
-  BPM_CU(cudaFuncSetAttribute((bpm_persistent_kernel<N, true, S>), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)r.smem_persist));
-  int per_sm = 0;
-  BPM_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bpm_persistent_kernel<N, false, S>, kThreads,
-                                                       r.smem_persist));
-  if (per_sm < 1) return fail(BPM_ERR_UNSUPPORTED, "persistent kernel for N=%d does not fit on an SM", N);
-  std::vector<float2> tw = twiddles_for<N, S>();
-  if (tw.size() != (size_t)cfg_twiddles<C>() || tw.empty())
-    return fail(BPM_ERR_UNSUPPORTED, "twiddle table size mismatch for N=%d", N);
-  r.sched = S;
+// schedules of the row and column lengths of instance i
+int row_sched_of(const bpm_plan_s* p, const bpm_instance_desc& d) {
+  if (p->inst.size() > 1) return 0;
+  return d.nx == d.ny ? p->sched : default_schedule(d.nx);
+}
+int col_sched_of(const bpm_plan_s* p, const bpm_instance_desc& d) {
+  if (p->inst.size() > 1) return 0;
+  return d.nx == d.ny ? p->sched : default_schedule(d.ny);
+}
+
+// The plan's resources for length n in schedule s: kernels' shared-memory
+// limits raised and the twiddle table uploaded (once per plan).
+int use_length(bpm_plan_s* p, int n, int s, LenRes** out) {
+  auto key = std::make_pair(n, s);
+  auto it = p->lens.find(key);
+  if (it != p->lens.end()) {
+    *out = &it->second;
+    return BPM_OK;
+  }
+  const LenOps* o = find_len_ops(n, s);
+  if (!o) return fail(BPM_ERR_UNSUPPORTED, "transform length %d has no schedule %d", n, s);
+  if (o->smem > p->max_optin || o->line_smem > p->max_optin)
+    return fail(BPM_ERR_UNSUPPORTED, "transform length %d needs more shared memory than the device has", n);
+  BPM_CU(o->init(o->smem, o->line_smem));
+  std::vector<float2> tw;
+  o->twiddles(tw);
+  if (tw.size() != (size_t)o->tw_count || tw.empty())
+    return fail(BPM_ERR_UNSUPPORTED, "twiddle table size mismatch for length %d", n);
+  LenRes r;
+  r.ops = o;
   BPM_CU(cudaMalloc(&r.tw, tw.size() * sizeof(float2)));
-  BPM_CU(cudaMemcpy(r.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  cudaError_t e = cudaMemcpy(r.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(r.tw);
+    return fail(BPM_ERR_CUDA, "twiddle upload failed: %s", cudaGetErrorString(e));
+  }
+  *out = &(p->lens[key] = r);
   return BPM_OK;
 }
 
-int setup_n(NRes& r, int n, int sms, int sched = 0) {
-  r.n = n;
-  if (sched < 0 || sched >= kSchedules(n)) return fail(BPM_ERR_ARG, "size %d has no schedule %d", n, sched);
-  switch (n * 4 + sched) {
-    case 64 * 4: return setup_kernels<64, 0>(r, sms);
-    case 128 * 4: return setup_kernels<128, 0>(r, sms);
-    case 192 * 4: return setup_kernels<192, 0>(r, sms);
-    case 256 * 4: return setup_kernels<256, 0>(r, sms);
-    case 256 * 4 + 1: return setup_kernels<256, 1>(r, sms);
-    case 256 * 4 + 2: return setup_kernels<256, 2>(r, sms);
-    case 384 * 4: return setup_kernels<384, 0>(r, sms);
-    case 512 * 4: return setup_kernels<512, 0>(r, sms);
-    case 512 * 4 + 1: return setup_kernels<512, 1>(r, sms);
-    case 512 * 4 + 2: return setup_kernels<512, 2>(r, sms);
-    case 1024 * 4: return setup_kernels<1024, 0>(r, sms);
-    case 1024 * 4 + 1: return setup_kernels<1024, 1>(r, sms);
+// Team and shared-memory staging of the persistent kernel of a grid: the
+// smallest team that gives every group one row and one column per half-step
+// (every SM takes rows with the four-step column layout), at most one CTA per
+// SM; the staging buffers of propagator columns, index rows and intensity rows
+// are dropped (in that order) when they would not fit next to the tables and
+// group buffers.
+void grid_config(const PairOps* o, int nx, int ny, int sms, size_t max_optin, GridRes& g) {
+  const int want = o->four_step ? ny : std::max((ny + o->row_ng - 1) / o->row_ng, (nx + o->col_ng - 1) / o->col_ng);
+  g.ops = o;
+  g.team = std::max(1, std::min(want, sms));
+  g.rmax_r = (ny + g.team - 1) / g.team;
+  const int cper = (nx + g.team - 1) / g.team;
+  g.rmax_c = (cper + o->col_ng - 1) / o->col_ng * o->col_ng;
+  auto rup = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  const size_t hb = rup((size_t)g.rmax_c * o->col_hs * sizeof(float2)), db = rup((size_t)g.rmax_r * nx * 2),
+               ib = rup((size_t)g.rmax_r * nx * sizeof(float));
+  const size_t budget = max_optin - 1024;   // static shared memory of the kernel
+  const size_t base = o->smem_base;
+  g.h_res = g.dn_stage = g.i_stage = 1;
+  if (base + hb + db + ib > budget) g.h_res = 0;
+  if (base + db + ib > budget) g.i_stage = 0;
+  if (base + db > budget) g.dn_stage = 0;
+  g.smem_persist = base + (g.h_res ? hb : 0) + (g.dn_stage ? db : 0) + (g.i_stage ? ib : 0);
+}
+
+// The persistent kernel of a single-field plan's grid in its schedule, when
+// one is compiled and fits: launch attributes, occupancy check and the
+// combined twiddle table.
+int setup_grid(bpm_plan_s* p) {
+  const bpm_instance_desc& d = p->inst[0].d;
+  GridRes& g = p->grid;
+  cudaFree(g.tw);
+  g = GridRes();
+  if (p->flags & BPM_FLAG_MULTI_LAUNCH) return BPM_OK;
+  const PairOps* o = find_pair_ops(d.nx, d.ny, d.nx == d.ny ? p->sched : 0);
+  if (!o) return BPM_OK;     // one launch per half-step
+  GridRes r;
+  grid_config(o, d.nx, d.ny, p->sms, p->max_optin, r);
+  if (r.smem_persist > p->max_optin - 1024) return BPM_OK;
+  for (int k = 0; k < 2; ++k)
+    BPM_CU(cudaFuncSetAttribute(o->kernel[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r.smem_persist));
+  int per_sm = 0;
+  BPM_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, o->kernel[0], kThreads, r.smem_persist));
+  if (per_sm < 1) return BPM_OK;
+  std::vector<float2> tw;
+  o->twiddles(tw);
+  if (tw.size() != (size_t)o->tw_count || tw.empty())
+    return fail(BPM_ERR_UNSUPPORTED, "twiddle table size mismatch for the %d x %d grid", d.nx, d.ny);
+  BPM_CU(cudaMalloc(&r.tw, tw.size() * sizeof(float2)));
+  cudaError_t e = cudaMemcpy(r.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(r.tw);
+    return fail(BPM_ERR_CUDA, "twiddle upload failed: %s", cudaGetErrorString(e));
   }
-  return fail(BPM_ERR_UNSUPPORTED, "grid size %d is not supported", n);
+  g = r;
+  return BPM_OK;
+}
+
+// Every length, schedule and grid resource of a single-field plan for its
+// current schedule.
+int setup_single(bpm_plan_s* p) {
+  const bpm_instance_desc& d = p->inst[0].d;
+  LenRes* lr = nullptr;
+  int rc = use_length(p, d.nx, row_sched_of(p, d), &lr);
+  if (rc == BPM_OK) rc = use_length(p, d.ny, col_sched_of(p, d), &lr);
+  if (rc == BPM_OK) rc = setup_grid(p);
+  return rc;
 }
 
 int check_desc(const bpm_instance_desc& d, int i) {
-  if (d.nx != d.ny)
-    return fail(BPM_ERR_UNSUPPORTED, "instance %d: nx (%d) != ny (%d) is not supported", i, d.nx, d.ny);
-  if (!supported_n(d.nx))
-    return fail(BPM_ERR_UNSUPPORTED, "instance %d: nx = %d is not one of 64,128,192,256,384,512,1024", i, d.nx);
+  if (!supported_len(d.nx) || !supported_len(d.ny))
+    return fail(BPM_ERR_UNSUPPORTED,
+                "instance %d: nx = %d or ny = %d is not one of 64, 96, 128, 192, 256, 384, 512, 768, 1024, "
+                "1536, 2048", i, d.nx, d.ny);
+  if ((long long)d.nx * d.ny > kMaxPixels)
+    return fail(BPM_ERR_UNSUPPORTED, "instance %d: nx ny = %lld exceeds 2^22", i, (long long)d.nx * d.ny);
   if (d.nz < 0) return fail(BPM_ERR_ARG, "instance %d: nz < 0", i);
   if (!(d.dx > 0) || !(d.dy > 0) || !(d.dz > 0) || !(d.lambda > 0) || !(d.n0 > 0) || !std::isfinite(d.dx) ||
       !std::isfinite(d.dy) || !std::isfinite(d.dz) || !std::isfinite(d.lambda) || !std::isfinite(d.n0))
@@ -273,22 +310,29 @@ int check_desc(const bpm_instance_desc& d, int i) {
   return BPM_OK;
 }
 
-// Rebuild the per-size resources of a single-field plan for schedule sched
-// (twiddle table and launch configuration; the propagator tables and the
-// synthesis scratch do not depend on it).
+// lengths the batched kernel is compiled for (square instances only)
+bool batch_size_ok(const bpm_instance_desc& d) {
+  if (d.nx != d.ny) return false;
+  switch (d.nx) {
+    case 64: case 128: case 192: case 256: case 384: case 512: case 1024: return true;
+    default: return false;
+  }
+}
+
+// Switch a single-field square plan to schedule sched (the twiddle tables of
+// the new schedule, the grid's launch configuration; the propagator tables and
+// the synthesis scratch do not depend on it).
 int switch_schedule(bpm_plan_s* p, int sched) {
-  NRes& cur = p->res.begin()->second;
-  if (cur.sched == sched) return BPM_OK;
-  NRes r;
-  int rc = setup_n(r, cur.n, p->sms, sched);
+  if (p->sched == sched) return BPM_OK;
+  const int keep = p->sched;
+  BPM_CU(cudaDeviceSynchronize());      // no launch of this plan may still read the old tables
+  p->sched = sched;
+  int rc = setup_single(p);
   if (rc) {
-    cudaFree(r.tw);
+    p->sched = keep;
+    setup_single(p);
     return rc;
   }
-  BPM_CU(cudaDeviceSynchronize());      // no launch of this plan may still read the old table
-  cudaFree(cur.tw);
-  r.tmp = cur.tmp;
-  cur = r;
   return BPM_OK;
 }
 
@@ -299,10 +343,9 @@ void free_plan(bpm_plan_s* p) {
     cudaFree(in.gt);
     cudaFree(in.delta);
   }
-  for (auto& kv : p->res) {
-    cudaFree(kv.second.tw);
-    cudaFree(kv.second.tmp);
-  }
+  for (auto& kv : p->lens) cudaFree(kv.second.tw);
+  for (auto& kv : p->tmp) cudaFree(kv.second);
+  cudaFree(p->grid.tw);
   cudaFree(p->bar);
   cudaFree(p->err);
   cudaFree(p->npupil);
@@ -332,11 +375,12 @@ void free_plan(bpm_plan_s* p) {
   delete p;
 }
 
-StepArgs base_args(bpm_plan_s* p, const InstPlan& in, const NRes& r) {
+StepArgs base_args(bpm_plan_s* p, const InstPlan& in) {
   StepArgs a;
   std::memset(&a, 0, sizeof a);
   a.ht = in.ht;
-  a.tw = r.tw;
+  a.nx = in.d.nx;
+  a.ny = in.d.ny;
   const double k0 = kTwoPi / in.d.lambda;
   a.screen_c = (float)(k0 * in.d.dz);
   a.k0n0 = k0 * in.d.n0;
@@ -347,87 +391,87 @@ StepArgs base_args(bpm_plan_s* p, const InstPlan& in, const NRes& r) {
   a.timeout_ns = p->timeout_ns;
   a.bar_extra = p->bar_extra;
   a.carrier = make_float2(1.f, 0.f);
-  a.rmax = r.rmax;
-  a.h_res = r.h_res;
-  a.dn_stage = r.dn_stage;
-  a.i_stage = r.i_stage;
   return a;
 }
 
 // ---- launches ---------------------------------------------------------------
 
-template <int N, int S>
-int launch_propagate(bpm_plan_s* p, const NRes& r, StepArgs a, cudaStream_t s) {
-  const int G = r.team;
-  if (p->flags & BPM_FLAG_MULTI_LAUNCH) {
-    bpm_row_kernel<N, ROW_FWD, false, S><<<G, kThreads, r.smem, s>>>(a, a.z_begin);
+// CTAs of a row (column) kernel: one group per row (column) and round at most
+// one CTA per SM
+int row_grid(const bpm_plan_s* p, const LenOps* o, int rows) {
+  return std::max(1, std::min(p->sms, (rows + o->NG - 1) / o->NG));
+}
+
+int lens_of(bpm_plan_s* p, const InstPlan& in, const LenRes** rl, const LenRes** cl) {
+  auto ir = p->lens.find(std::make_pair(in.d.nx, row_sched_of(p, in.d)));
+  auto ic = p->lens.find(std::make_pair(in.d.ny, col_sched_of(p, in.d)));
+  if (ir == p->lens.end() || ic == p->lens.end())
+    return fail(BPM_ERR_UNSUPPORTED, "grid %d x %d has no kernels in this plan", in.d.nx, in.d.ny);
+  *rl = &ir->second;
+  *cl = &ic->second;
+  return BPM_OK;
+}
+
+int launch_propagate(bpm_plan_s* p, const InstPlan& in, StepArgs a, cudaStream_t s) {
+  const GridRes& g = p->grid;
+  if (!g.ops) {
+    // one launch per half-step: rows with the row length's kernels and table,
+    // columns with the column length's
+    const LenRes *rl, *cl;
+    int rc = lens_of(p, in, &rl, &cl);
+    if (rc) return rc;
+    const int gr = row_grid(p, rl->ops, in.d.ny), gc = row_grid(p, cl->ops, in.d.nx);
+    StepArgs ar = a, ac = a;
+    ar.tw = rl->tw;
+    ac.tw = cl->tw;
+    ac.flip_col = rl->ops->loop != cl->ops->loop;
+    BPM_CU(rl->ops->row(ROW_FWD, false, gr, ar, a.z_begin, s));
     for (int zi = a.z_begin; zi < a.z_end; ++zi) {
       const int z = a.reverse ? a.z_begin + a.z_end - 1 - zi : zi;     // slice crossed by this step
-      bpm_col_kernel<N, COL_PROP, S><<<G, kThreads, r.smem, s>>>(a, z);
+      BPM_CU(cl->ops->col(COL_PROP, gc, ac, z, s));
       const bool last = zi + 1 == a.z_end;
-      if (a.kappa) {
-        if (!last) bpm_row_kernel<N, ROW_STEP, true, S><<<G, kThreads, r.smem, s>>>(a, z);
-        else bpm_row_kernel<N, ROW_LAST, true, S><<<G, kThreads, r.smem, s>>>(a, z);
-      } else {
-        if (!last) bpm_row_kernel<N, ROW_STEP, false, S><<<G, kThreads, r.smem, s>>>(a, z);
-        else bpm_row_kernel<N, ROW_LAST, false, S><<<G, kThreads, r.smem, s>>>(a, z);
-      }
+      BPM_CU(rl->ops->row(last ? ROW_LAST : ROW_STEP, a.kappa != nullptr, gr, ar, z, s));
     }
-    BPM_CU(cudaGetLastError());
     return BPM_OK;
   }
+  a.tw = g.tw;
+  a.rmax_r = g.rmax_r;
+  a.rmax_c = g.rmax_c;
+  a.h_res = g.h_res;
+  a.dn_stage = g.dn_stage;
+  a.i_stage = g.i_stage;
   BPM_CU(cudaMemsetAsync(p->bar, 0, sizeof(unsigned), s));
   void* args[] = {&a};
-  const void* fn = a.kappa ? (const void*)bpm_persistent_kernel<N, true, S> : (const void*)bpm_persistent_kernel<N, false, S>;
-  BPM_CU(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kThreads), args, r.smem_persist, s));
+  BPM_CU(cudaLaunchCooperativeKernel(g.ops->kernel[a.kappa ? 1 : 0], dim3(g.team), dim3(kThreads), args,
+                                     g.smem_persist, s));
   return BPM_OK;
 }
 
-template <int N, int S>
-int launch_synth_group(bpm_plan_s*, const NRes& r, StepArgs a, cudaStream_t s) {
-  const int G = r.team;
-  bpm_row_kernel<N, ROW_FWD, false, S><<<G, kThreads, r.smem, s>>>(a, 0);
-  bpm_col_kernel<N, COL_FOCUS, S><<<G, kThreads, r.smem, s>>>(a, 0);
-  bpm_row_kernel<N, ROW_INV_ACC, false, S><<<G, kThreads, r.smem, s>>>(a, 0);
-  BPM_CU(cudaGetLastError());
+// multiplexed synthesis of one focal-depth group: forward 2D DFT of the
+// scattered emitters, focusing filter, inverse DFT accumulated into the output
+int launch_synth_group(bpm_plan_s* p, const InstPlan& in, StepArgs a, cudaStream_t s) {
+  const LenRes *rl, *cl;
+  int rc = lens_of(p, in, &rl, &cl);
+  if (rc) return rc;
+  const int gr = row_grid(p, rl->ops, in.d.ny), gc = row_grid(p, cl->ops, in.d.nx);
+  StepArgs ar = a, ac = a;
+  ar.tw = rl->tw;
+  ac.tw = cl->tw;
+  BPM_CU(rl->ops->row(ROW_FWD, false, gr, ar, 0, s));
+  BPM_CU(cl->ops->col(COL_FOCUS, gc, ac, 0, s));
+  BPM_CU(rl->ops->row(ROW_INV_ACC, false, gr, ar, 0, s));
   return BPM_OK;
 }
 
-template <int N, int S>
-int launch_light_sheet(bpm_plan_s* p, const NRes& r, StepArgs a, double w0, double xc, cudaStream_t s) {
-  using C = Cfg<N, S>;
-  const int grid = std::max(1, std::min(p->sms, (N * N + 4 * kThreads - 1) / (4 * kThreads)));
-  bpm_light_sheet_kernel<N, S><<<grid, kThreads, r.smem + C::GS * sizeof(float2), s>>>(a, w0, xc);
-  BPM_CU(cudaGetLastError());
+int launch_light_sheet(bpm_plan_s* p, const InstPlan& in, StepArgs a, double w0, double xc, cudaStream_t s) {
+  const LenRes *rl, *cl;
+  int rc = lens_of(p, in, &rl, &cl);
+  if (rc) return rc;
+  a.tw = rl->tw;
+  const long long M = (long long)in.d.nx * in.d.ny;
+  const int grid = (int)std::max(1ll, std::min<long long>(p->sms, (M + 4 * kThreads - 1) / (4 * kThreads)));
+  BPM_CU(rl->ops->light_sheet(grid, a, w0, xc, s));
   return BPM_OK;
-}
-
-// call with the size N and schedule S of r as compile-time constants
-#define BPM_DISPATCH(r, call)                                                 \
-  switch ((r).n * 4 + (r).sched) {                                            \
-    case 64 * 4: { constexpr int N = 64, S = 0; return call; }                \
-    case 128 * 4: { constexpr int N = 128, S = 0; return call; }              \
-    case 192 * 4: { constexpr int N = 192, S = 0; return call; }              \
-    case 256 * 4: { constexpr int N = 256, S = 0; return call; }              \
-    case 256 * 4 + 1: { constexpr int N = 256, S = 1; return call; }          \
-    case 256 * 4 + 2: { constexpr int N = 256, S = 2; return call; }          \
-    case 384 * 4: { constexpr int N = 384, S = 0; return call; }              \
-    case 512 * 4: { constexpr int N = 512, S = 0; return call; }              \
-    case 512 * 4 + 1: { constexpr int N = 512, S = 1; return call; }          \
-    case 512 * 4 + 2: { constexpr int N = 512, S = 2; return call; }          \
-    case 1024 * 4: { constexpr int N = 1024, S = 0; return call; }            \
-    case 1024 * 4 + 1: { constexpr int N = 1024, S = 1; return call; }        \
-  }                                                                           \
-  return fail(BPM_ERR_UNSUPPORTED, "grid size %d (schedule %d) is not supported", (r).n, (r).sched);
-
-int dispatch_propagate(bpm_plan_s* p, const NRes& r, const StepArgs& a, cudaStream_t s) {
-  BPM_DISPATCH(r, (launch_propagate<N, S>(p, r, a, s)))
-}
-int dispatch_synth(bpm_plan_s* p, const NRes& r, const StepArgs& a, cudaStream_t s) {
-  BPM_DISPATCH(r, (launch_synth_group<N, S>(p, r, a, s)))
-}
-int dispatch_light_sheet(bpm_plan_s* p, const NRes& r, const StepArgs& a, double w0, double xc, cudaStream_t s) {
-  BPM_DISPATCH(r, (launch_light_sheet<N, S>(p, r, a, w0, xc, s)))
 }
 
 int finish_call(bpm_plan_s* p, cudaStream_t s) {
@@ -456,17 +500,17 @@ int max_active_clusters(bpm_plan_s* p, int cl, int* out) {
   cfg.dynamicSmemBytes = p->batch_smem;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  BPM_CU(cudaOccupancyMaxActiveClusters(out, (void*)bpm_batch_kernel, &cfg));
+  BPM_CU(cudaOccupancyMaxActiveClusters(out, batch_kernel_fn(), &cfg));
   return BPM_OK;
 }
 
 int setup_batch(bpm_plan_s* p) {
   const int n = (int)p->inst.size();
   size_t smem = 0;
-  for (auto& kv : p->res) smem = std::max(smem, kv.second.smem);
+  for (auto& kv : p->lens) smem = std::max(smem, kv.second.ops->smem);
   p->batch_smem = smem;
-  BPM_CU(cudaFuncSetAttribute(bpm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  BPM_CU(cudaFuncSetAttribute(bpm_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  BPM_CU(cudaFuncSetAttribute(batch_kernel_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BPM_CU(cudaFuncSetAttribute(batch_kernel_fn(), cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   BPM_CU(cudaMalloc(&p->d_inst, sizeof(InstArgs) * n));
   BPM_CU(cudaMalloc(&p->d_order, sizeof(int) * n));
   BPM_CU(cudaMalloc(&p->d_queue, sizeof(unsigned long long)));
@@ -543,7 +587,8 @@ int enqueue_batch(bpm_plan_s* p, int clusters, cudaStream_t s) {
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  BPM_CU(cudaLaunchKernelEx(&cfg, bpm_batch_kernel, b));
+  void* kargs[] = {&b};
+  BPM_CU(cudaLaunchKernelExC(&cfg, batch_kernel_fn(), kargs));
   if (use_fill) {
     BPM_CU(cudaStreamWaitEvent(p->fill_stream, p->ev_fork, 0));
     BatchArgs f = b;
@@ -553,7 +598,8 @@ int enqueue_batch(bpm_plan_s* p, int clusters, cudaStream_t s) {
     attr[0].val.clusterDim.x = kFillCluster;
     cfg.gridDim = dim3(fill * kFillCluster);
     cfg.stream = p->fill_stream;
-    BPM_CU(cudaLaunchKernelEx(&cfg, bpm_batch_kernel, f));
+    void* fargs[] = {&f};
+    BPM_CU(cudaLaunchKernelExC(&cfg, batch_kernel_fn(), fargs));
     BPM_CU(cudaEventRecord(p->ev_join, p->fill_stream));
     BPM_CU(cudaStreamWaitEvent(s, p->ev_join, 0));
   }
@@ -568,7 +614,7 @@ int propagate_batch(bpm_plan_s* p, const void* const* d_dn, const void* const* d
   std::memset(args.data(), 0, sizeof(InstArgs) * n);
   for (int i = 0; i < n; ++i) {
     const InstPlan& in = p->inst[i];
-    const NRes& r = p->res[in.d.nx];
+    const LenRes& r = p->lens[std::make_pair(in.d.nx, 0)];
     InstArgs& a = args[i];
     a.work = static_cast<float2*>(d_Eout[i]);
     a.ein = static_cast<const float2*>(d_Ein[i]);
@@ -639,6 +685,10 @@ extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_in
   for (int i = 0; i < n_inst; ++i) {
     int rc = check_desc(inst[i], i);
     if (rc) return rc;
+    if (n_inst > 1 && !batch_size_ok(inst[i]))
+      return fail(BPM_ERR_UNSUPPORTED,
+                  "instance %d: batched plans take square grids of 64, 128, 192, 256, 384, 512 or 1024 (got %d x %d)",
+                  i, inst[i].nx, inst[i].ny);
   }
   bpm_plan_s* p = new (std::nothrow) bpm_plan_s;
   if (!p) return fail(BPM_ERR_ARG, "out of host memory");
@@ -648,8 +698,12 @@ extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_in
     if (e != cudaSuccess && rc == BPM_OK) rc = fail(BPM_ERR_CUDA, "%s failed: %s", what, cudaGetErrorString(e));
     return e == cudaSuccess;
   };
+  int optin = 0;
   cu(cudaGetDevice(&p->dev), "cudaGetDevice");
   if (rc == BPM_OK) cu(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->dev), "cudaDeviceGetAttribute");
+  if (rc == BPM_OK)
+    cu(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->dev), "cudaDeviceGetAttribute");
+  p->max_optin = (size_t)optin;
   if (rc == BPM_OK) cu(cudaMalloc(&p->bar, 64), "cudaMalloc(barrier)");
   if (rc == BPM_OK) cu(cudaMalloc(&p->err, sizeof(int)), "cudaMalloc(error word)");
   if (rc == BPM_OK) cu(cudaMalloc(&p->npupil, sizeof(unsigned long long)), "cudaMalloc(pupil count)");
@@ -657,14 +711,7 @@ extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_in
   for (int i = 0; i < n_inst && rc == BPM_OK; ++i) {
     InstPlan ip;
     ip.d = inst[i];
-    const int n = inst[i].nx;
-    if (!p->res.count(n)) {
-      NRes r;
-      rc = setup_n(r, n, p->sms, n_inst == 1 ? kDefaultSchedule(n) : 0);
-      p->res[n] = r;
-      if (rc) break;
-    }
-    const size_t M = (size_t)n * n;
+    const size_t M = (size_t)inst[i].nx * inst[i].ny;
     if (!cu(cudaMalloc(&ip.ht, M * sizeof(float2)), "cudaMalloc(propagator)")) break;
     if (flags & BPM_FLAG_ADAPTIVE) {
       if (!cu(cudaMalloc(&ip.gt, M * sizeof(float)), "cudaMalloc(adapted propagator rates)")) {
@@ -688,7 +735,19 @@ extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_in
       cu(cudaGetLastError(), "bpm_build_gt_kernel");
     }
   }
-  if (rc == BPM_OK && n_inst > 1) rc = setup_batch(p);
+  if (rc == BPM_OK) {
+    if (n_inst == 1) {
+      const bpm_instance_desc& d = inst[0];
+      p->sched = d.nx == d.ny ? default_schedule(d.nx) : 0;
+      rc = setup_single(p);
+    } else {
+      for (int i = 0; i < n_inst && rc == BPM_OK; ++i) {
+        LenRes* lr = nullptr;
+        rc = use_length(p, inst[i].nx, 0, &lr);
+      }
+      if (rc == BPM_OK) rc = setup_batch(p);
+    }
+  }
   if (rc == BPM_OK) cu(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
   if (rc != BPM_OK) {
     free_plan(p);
@@ -732,7 +791,6 @@ int propagate_impl(bpm_plan_t p, const void* const* d_dn, const void* const* d_E
   }
   for (size_t i = 0; i < p->inst.size(); ++i) {
     const InstPlan& in = p->inst[i];
-    const NRes& r = p->res[in.d.nx];
     const int zb = std::min(z_begin, in.d.nz), ze = std::min(z_end, in.d.nz);
     const size_t bytes = (size_t)in.d.nx * in.d.ny * sizeof(float2);
     if (ze == zb) {
@@ -740,7 +798,7 @@ int propagate_impl(bpm_plan_t p, const void* const* d_dn, const void* const* d_E
         BPM_CU(cudaMemcpyAsync(d_Eout[i], d_Ein[i], bytes, cudaMemcpyDeviceToDevice, stream));
       continue;
     }
-    StepArgs a = base_args(p, in, r);
+    StepArgs a = base_args(p, in);
     a.work = static_cast<float2*>(d_Eout[i]);
     a.ein = static_cast<const float2*>(d_Ein[i]);
     a.dn = static_cast<const __half*>(d_dn[i]);
@@ -763,7 +821,7 @@ int propagate_impl(bpm_plan_t p, const void* const* d_dn, const void* const* d_E
     const double k0 = kTwoPi / in.d.lambda;
     double ph = std::fmod(k0 * in.d.n0 * in.d.dz * (double)(ze - zb), kTwoPi);
     a.carrier = make_float2((float)std::cos(ph), (float)std::sin(ph));
-    int rc = dispatch_propagate(p, r, a, stream);
+    int rc = launch_propagate(p, in, a, stream);
     if (rc) return rc;
   }
   return finish_call(p, stream);
@@ -825,10 +883,10 @@ extern "C" int bpm_demultiplex(bpm_plan_t p, int inst, const float* d_I, int w_b
     return fail(BPM_ERR_ARG, "patch sizes must be positive and hold at most 2^30 voxels");
   if (n_foci == 0) return finish_call(p, stream);
   if (!h_foci || !d_out || (w_nz > 0 && !d_I)) return fail(BPM_ERR_ARG, "NULL pointer");
-  const int n = p->inst[inst].d.nx;
+  const int nx = p->inst[inst].d.nx, ny = p->inst[inst].d.ny;
   for (int j = 0; j < n_foci; ++j) {
     const int x = h_foci[3 * j], y = h_foci[3 * j + 1];
-    if (x < 0 || x >= n || y < 0 || y >= n) return fail(BPM_ERR_ARG, "focus %d lies outside the grid", j);
+    if (x < 0 || x >= nx || y < 0 || y >= ny) return fail(BPM_ERR_ARG, "focus %d lies outside the grid", j);
   }
   if ((int)(3 * (size_t)n_foci) > p->demux_cap) {
     BPM_CU(cudaStreamSynchronize(stream));
@@ -844,7 +902,8 @@ extern "C" int bpm_demultiplex(bpm_plan_t p, int inst, const float* d_I, int w_b
   BPM_CU(cudaMemcpyAsync(p->demux_foci, foci.data(), foci.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
   const long long total = (long long)px * py * pz * n_foci;
   const int grid = (int)std::min<long long>((total + kThreads - 1) / kThreads, (long long)p->sms * 16);
-  bpm_demux_kernel<<<grid, kThreads, 0, stream>>>(d_I, n, w_begin, w_nz, p->demux_foci, n_foci, px, py, pz, d_out);
+  bpm_demux_kernel<<<grid, kThreads, 0, stream>>>(d_I, nx, ny, w_begin, w_nz, p->demux_foci, n_foci, px, py, pz,
+                                                  d_out);
   BPM_CU(cudaGetLastError());
   return finish_call(p, stream);
 }
@@ -862,9 +921,8 @@ int multiplex_impl(bpm_plan_t p, int inst, int n_foci, const double* h_xyz, cons
   if (!d_Eout) return fail(BPM_ERR_ARG, "d_Eout is NULL");
   if (!aligned16(d_Eout)) return fail(BPM_ERR_ALIGN, "d_Eout must be 16-byte aligned");
   const InstPlan& in = p->inst[inst];
-  NRes& r = p->res[in.d.nx];
-  const int n = in.d.nx;
-  const size_t M = (size_t)n * n;
+  const int nx = in.d.nx, ny = in.d.ny;
+  const size_t M = (size_t)nx * ny;
   // emitters on the grid, grouped by focal depth (stable order within a group)
   std::vector<int> order;
   for (int j = 0; j < n_foci; ++j) {
@@ -872,7 +930,7 @@ int multiplex_impl(bpm_plan_t p, int inst, int n_foci, const double* h_xyz, cons
     if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z) || !std::isfinite(h_phase[j]))
       return fail(BPM_ERR_ARG, "emitter %d has a non-finite coordinate or phase", j);
     const double fx = std::floor(x / in.d.dx + 0.5), fy = std::floor(y / in.d.dy + 0.5);
-    if (fx < 0 || fx >= n || fy < 0 || fy >= n) continue;
+    if (fx < 0 || fx >= nx || fy < 0 || fy >= ny) continue;
     order.push_back(j);
   }
   std::stable_sort(order.begin(), order.end(),
@@ -892,13 +950,14 @@ int multiplex_impl(bpm_plan_t p, int inst, int n_foci, const double* h_xyz, cons
     BPM_CU(cudaMalloc(&p->foci_phase, order.size() * sizeof(double)));
     p->foci_cap = (int)order.size();
   }
-  if (!r.tmp) BPM_CU(cudaMalloc(&r.tmp, M * sizeof(float2)));
+  float2*& tmp = p->tmp[std::make_pair(nx, ny)];
+  if (!tmp) BPM_CU(cudaMalloc(&tmp, M * sizeof(float2)));
   std::vector<int> idx;
   std::vector<double> ph, zs;
   for (int j : order) {
     const int fx = (int)std::floor(h_xyz[3 * j] / in.d.dx + 0.5);
     const int fy = (int)std::floor(h_xyz[3 * j + 1] / in.d.dy + 0.5);
-    idx.push_back(fy * n + fx);
+    idx.push_back(fy * nx + fx);
     ph.push_back(h_phase[j]);
     zs.push_back(h_xyz[3 * j + 2]);
   }
@@ -909,11 +968,11 @@ int multiplex_impl(bpm_plan_t p, int inst, int n_foci, const double* h_xyz, cons
   const double k0 = kTwoPi / in.d.lambda;
   const double kna = k0 * NA;
   const double kin = k0 * NA_in;
-  StepArgs a = base_args(p, in, r);
+  StepArgs a = base_args(p, in);
   a.kna2 = kna * kna;
   a.kin2 = kin * kin;
   BPM_CU(cudaMemsetAsync(p->npupil, 0, sizeof(unsigned long long), stream));
-  bpm_pupil_count_kernel<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>(n, in.d.dx, in.d.dy, a.k0n0, a.kin2,
+  bpm_pupil_count_kernel<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>(nx, ny, in.d.dx, in.d.dy, a.k0n0, a.kin2,
                                                                          a.kna2, p->npupil);
   BPM_CU(cudaGetLastError());
   size_t g0 = 0;
@@ -921,17 +980,17 @@ int multiplex_impl(bpm_plan_t p, int inst, int n_foci, const double* h_xyz, cons
   while (g0 < idx.size()) {
     size_t g1 = g0;
     while (g1 < idx.size() && zs[g1] == zs[g0]) ++g1;
-    BPM_CU(cudaMemsetAsync(r.tmp, 0, M * sizeof(float2), stream));
+    BPM_CU(cudaMemsetAsync(tmp, 0, M * sizeof(float2), stream));
     const int cnt = (int)(g1 - g0);
-    bpm_scatter_kernel<<<(cnt + 127) / 128, 128, 0, stream>>>(r.tmp, n, p->foci_idx + g0, p->foci_phase + g0, cnt,
-                                                              p->npupil);
+    bpm_scatter_kernel<<<(cnt + 127) / 128, 128, 0, stream>>>(tmp, nx, ny, p->foci_idx + g0, p->foci_phase + g0,
+                                                              cnt, p->npupil);
     BPM_CU(cudaGetLastError());
-    a.work = r.tmp;
-    a.ein = r.tmp;
+    a.work = tmp;
+    a.ein = tmp;
     a.out = static_cast<float2*>(d_Eout);
     a.zf = zs[g0];
     a.accumulate = group > 0;
-    int rc = dispatch_synth(p, r, a, stream);
+    int rc = launch_synth_group(p, in, a, stream);
     if (rc) return rc;
     g0 = g1;
     ++group;
@@ -959,13 +1018,12 @@ extern "C" int bpm_light_sheet(bpm_plan_t p, int inst, double NA, double zf, voi
   if (!d_Eout) return fail(BPM_ERR_ARG, "d_Eout is NULL");
   if (!aligned16(d_Eout)) return fail(BPM_ERR_ALIGN, "d_Eout must be 16-byte aligned");
   const InstPlan& in = p->inst[inst];
-  const NRes& r = p->res[in.d.nx];
-  StepArgs a = base_args(p, in, r);
+  StepArgs a = base_args(p, in);
   a.work = static_cast<float2*>(d_Eout);
   a.zf = zf;
   const double w0 = in.d.lambda / (M_PI * NA);
   const double xc = (double)(in.d.nx / 2) * in.d.dx;
-  int rc = dispatch_light_sheet(p, r, a, w0, xc, stream);
+  int rc = launch_light_sheet(p, in, a, w0, xc, stream);
   if (rc) return rc;
   return finish_call(p, stream);
 }
@@ -996,11 +1054,21 @@ extern "C" const char* bpm_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int bpm_plan_info(bpm_plan_t p, int* out, int n_out) {
   if (!p || !out || n_out < 0) return fail(BPM_ERR_ARG, "bad arguments");
-  const NRes& r = p->res.begin()->second;
-  const bool multi = (p->flags & BPM_FLAG_MULTI_LAUNCH) != 0;
-  const int nz = p->inst[0].d.nz;
-  int vals[7] = {r.team, kThreads, (int)(multi ? r.smem : r.smem_persist), multi ? 0 : 1, multi ? 1 + 2 * nz : 1,
-                 r.sched, kSchedules(r.n)};
+  const bpm_instance_desc& d = p->inst[0].d;
+  const bool persist = p->grid.ops != nullptr;
+  const int nz = d.nz;
+  int vals[7] = {0, kThreads, 0, persist ? 1 : 0, persist ? 1 : 1 + 2 * nz, p->sched,
+                 d.nx == d.ny ? schedule_count(d.nx) : 1};
+  if (persist) {
+    vals[0] = p->grid.team;
+    vals[2] = (int)p->grid.smem_persist;
+  } else {
+    const LenRes *rl, *cl;
+    if (lens_of(p, p->inst[0], &rl, &cl) == BPM_OK) {
+      vals[0] = row_grid(p, rl->ops, d.ny);
+      vals[2] = (int)std::max(rl->ops->smem, cl->ops->smem);
+    }
+  }
   if (p->inst.size() > 1) {
     vals[0] = p->cluster;
     vals[2] = (int)p->batch_smem;
@@ -1094,9 +1162,10 @@ namespace {
 // and keep the fastest.
 int autotune_schedule(bpm_plan_s* p, const void* const* d_dn, const void* const* d_Ein, void* const* d_Eout,
                       float* const* d_I, int z_probe, cudaStream_t stream) {
-  const int n = p->inst[0].d.nx, count = kSchedules(n);
+  const bpm_instance_desc& d = p->inst[0].d;
+  const int count = d.nx == d.ny ? schedule_count(d.nx) : 1;
   if (count < 2) return BPM_OK;
-  const int keep = p->res.begin()->second.sched;
+  const int keep = p->sched;
   float best = 1e30f;
   int best_s = keep;
   cudaEvent_t e0, e1;
@@ -1131,9 +1200,10 @@ int autotune_schedule(bpm_plan_s* p, const void* const* d_dn, const void* const*
 extern "C" int bpm_set_schedule(bpm_plan_t p, int schedule) {
   if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
   if (p->inst.size() != 1) return fail(BPM_ERR_UNSUPPORTED, "schedules are chosen for single-field plans only");
-  const int n = p->inst[0].d.nx;
-  if (schedule < 0 || schedule >= kSchedules(n))
-    return fail(BPM_ERR_ARG, "size %d has schedules 0..%d, not %d", n, kSchedules(n) - 1, schedule);
+  const bpm_instance_desc& d = p->inst[0].d;
+  const int count = d.nx == d.ny ? schedule_count(d.nx) : 1;
+  if (schedule < 0 || schedule >= count)
+    return fail(BPM_ERR_ARG, "grid %d x %d has schedules 0..%d, not %d", d.nx, d.ny, count - 1, schedule);
   return switch_schedule(p, schedule);
 }
 
@@ -1244,17 +1314,6 @@ __global__ void bpm_static_twiddle_kernel(float2* out, TwSchedule s) {
   out[(size_t)(p - 1) * s.n + twiddle_slot(b, r, t, R, s.t, s.paired != 0)] = make_float2((float)cs, (float)sn);
 }
 
-template <class RS>
-TwSchedule schedule_of(int n, int t, int sign) {
-  TwSchedule s{};
-  s.n = n;
-  s.t = t;
-  s.count = RS::count;
-  s.sign = sign;
-  for (int i = 0; i < RS::count && i < 4; ++i) s.r[i] = RS::at(i);
-  return s;
-}
-
 int launch_static_twiddles(const TwSchedule& s, float2* dst, cudaStream_t stream) {
   const int total = (s.count - 1) * s.n;
   if (total <= 0) return BPM_OK;
@@ -1263,32 +1322,21 @@ int launch_static_twiddles(const TwSchedule& s, float2* dst, cudaStream_t stream
   return BPM_OK;
 }
 
-template <int N>
 int static_propagate(const bpm_instance_desc& d, unsigned char* scratch, const void* d_dn, const void* d_Ein,
                      void* d_Eout, float* d_I, int zb, int ze, cudaStream_t stream) {
-  using C = Cfg<N>;
-  static_assert(cfg_twiddles<C>() <= (int)kStaticTwiddleFloat2 && C::TW4 == 0, "twiddle region too small");
-  // launch configuration: the same rule as a plan's (setup_kernels)
+  const int N = d.nx;
+  const LenOps* lo = find_len_ops(N, 0);
+  const PairOps* po = find_pair_ops(N, N, 0);
+  if (!lo || !po || lo->four_step || po->tw_count > (int)kStaticTwiddleFloat2)
+    return fail(BPM_ERR_UNSUPPORTED, "grid size %d is not supported", N);
+  // launch configuration: the same rule as a plan's (grid_config)
   int sms = 0, dev = 0, max_optin = 0;
   BPM_CU(cudaGetDevice(&dev));
   BPM_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   BPM_CU(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  NRes r;
-  r.n = N;
-  r.smem = cfg_smem_bytes<C>();
-  r.team = std::max(1, std::min((N + C::NG - 1) / C::NG, sms));
-  r.rmax = (N + r.team - 1) / r.team;
-  auto rup = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  const size_t hb = rup((size_t)r.rmax * C::HS * sizeof(float2)), db = rup((size_t)r.rmax * N * 2),
-               ib = rup((size_t)r.rmax * N * sizeof(float));
-  const size_t budget = (size_t)max_optin - 1024;
-  r.h_res = r.dn_stage = r.i_stage = 1;
-  if (r.smem + hb + db + ib > budget) r.h_res = 0;
-  if (r.smem + db + ib > budget) r.i_stage = 0;
-  if (r.smem + db > budget) r.dn_stage = 0;
-  r.smem_persist = r.smem + (r.h_res ? hb : 0) + (r.dn_stage ? db : 0) + (r.i_stage ? ib : 0);
-  BPM_CU(cudaFuncSetAttribute(bpm_persistent_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)r.smem_persist));
+  GridRes r;
+  grid_config(po, N, N, sms, (size_t)max_optin, r);
+  BPM_CU(cudaFuncSetAttribute(po->kernel[0], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r.smem_persist));
   unsigned* bar = reinterpret_cast<unsigned*>(scratch);
   int* err = reinterpret_cast<int*>(scratch + 64);
   float2* tw = reinterpret_cast<float2*>(scratch + kStaticWordsBytes);
@@ -1297,18 +1345,29 @@ int static_propagate(const bpm_instance_desc& d, unsigned char* scratch, const v
   // and the error word, rebuild both tables
   BPM_CU(cudaMemsetAsync(scratch, 0, kStaticWordsBytes, stream));
   int rc;
-  if constexpr (C::kLoop) {
+  if (lo->loop) {
     TwSchedule s{};
     s.n = N;
-    s.t = C::T;
-    s.count = C::E::NP;
+    s.t = lo->T;
+    s.count = lo->loop_passes;
     s.sign = -1;
     s.paired = 1;
-    for (int i = 0; i < C::E::NP && i < 4; ++i) s.r[i] = C::E::R;
+    for (int i = 0; i < lo->loop_passes && i < 4; ++i) s.r[i] = lo->loop_radix;
     rc = launch_static_twiddles(s, tw, stream);
   } else {
-    rc = launch_static_twiddles(schedule_of<typename C::F::Rad>(N, C::T, -1), tw, stream);
-    if (rc == BPM_OK) rc = launch_static_twiddles(schedule_of<typename C::I::Rad>(N, C::T, +1), tw + C::TWF, stream);
+    TwSchedule f{}, v{};
+    f.n = v.n = N;
+    f.t = v.t = lo->T;
+    f.count = lo->nf;
+    f.sign = -1;
+    v.count = lo->ni;
+    v.sign = +1;
+    for (int i = 0; i < 4; ++i) {
+      f.r[i] = lo->rf[i];
+      v.r[i] = lo->ri[i];
+    }
+    rc = launch_static_twiddles(f, tw, stream);
+    if (rc == BPM_OK) rc = launch_static_twiddles(v, tw + (size_t)(lo->nf - 1) * N, stream);
   }
   if (rc) return rc;
   const size_t M = (size_t)N * N;
@@ -1319,6 +1378,8 @@ int static_propagate(const bpm_instance_desc& d, unsigned char* scratch, const v
   std::memset(&a, 0, sizeof a);
   a.ht = ht;
   a.tw = tw;
+  a.nx = d.nx;
+  a.ny = d.ny;
   const double k0 = kTwoPi / d.lambda;
   a.screen_c = (float)(k0 * d.dz);
   a.k0n0 = k0 * d.n0;
@@ -1327,7 +1388,8 @@ int static_propagate(const bpm_instance_desc& d, unsigned char* scratch, const v
   a.bar = bar;
   a.err = err;
   a.timeout_ns = 2000000000ull;
-  a.rmax = r.rmax;
+  a.rmax_r = r.rmax_r;
+  a.rmax_c = r.rmax_c;
   a.h_res = r.h_res;
   a.dn_stage = r.dn_stage;
   a.i_stage = r.i_stage;
@@ -1342,8 +1404,7 @@ int static_propagate(const bpm_instance_desc& d, unsigned char* scratch, const v
   const double ph = std::fmod(k0 * d.n0 * d.dz * (double)(ze - zb), kTwoPi);
   a.carrier = make_float2((float)std::cos(ph), (float)std::sin(ph));
   void* args[] = {&a};
-  BPM_CU(cudaLaunchCooperativeKernel((const void*)bpm_persistent_kernel<N>, dim3(r.team), dim3(kThreads), args,
-                                     r.smem_persist, stream));
+  BPM_CU(cudaLaunchCooperativeKernel(po->kernel[0], dim3(r.team), dim3(kThreads), args, r.smem_persist, stream));
   BPM_CU(cudaStreamSynchronize(stream));
   int e = 0;
   BPM_CU(cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1360,9 +1421,9 @@ extern "C" int bpm_propagate_static(const bpm_instance_desc* inst, const void* d
   if (!inst) return fail(BPM_ERR_ARG, "inst is NULL");
   int rc = check_desc(*inst, 0);
   if (rc) return rc;
-  if (inst->nx > kStaticMaxN)
+  if (inst->nx != inst->ny || inst->nx > kStaticMaxN)
     return fail(BPM_ERR_UNSUPPORTED,
-                "bpm_propagate_static handles grids up to %d x %d (its fixed device scratch is %zu bytes); "
+                "bpm_propagate_static handles square grids up to %d x %d (its fixed device scratch is %zu bytes); "
                 "got %d x %d, use bpm_plan/bpm_propagate", kStaticMaxN, kStaticMaxN, kStaticScratchBytes,
                 inst->nx, inst->ny);
   if (z_begin < 0 || z_end < z_begin) return fail(BPM_ERR_ARG, "need 0 <= z_begin <= z_end");
@@ -1390,11 +1451,5 @@ extern "C" int bpm_propagate_static(const bpm_instance_desc* inst, const void* d
     BPM_CU(cudaStreamSynchronize(stream));
     return BPM_OK;
   }
-  switch (inst->nx) {
-    case 64: return static_propagate<64>(*inst, scratch, d_dn, d_Ein, d_Eout, d_I, zb, ze, stream);
-    case 128: return static_propagate<128>(*inst, scratch, d_dn, d_Ein, d_Eout, d_I, zb, ze, stream);
-    case 192: return static_propagate<192>(*inst, scratch, d_dn, d_Ein, d_Eout, d_I, zb, ze, stream);
-    case 256: return static_propagate<256>(*inst, scratch, d_dn, d_Ein, d_Eout, d_I, zb, ze, stream);
-  }
-  return fail(BPM_ERR_UNSUPPORTED, "grid size %d is not supported", inst->nx);
+  return static_propagate(*inst, scratch, d_dn, d_Ein, d_Eout, d_I, zb, ze, stream);
 }

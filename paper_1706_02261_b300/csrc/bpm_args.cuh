@@ -1,0 +1,106 @@
+// bpm_args.cuh - argument blocks shared by the host side (bpm.cu) and the
+// device code of the split-step beam-propagation library.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bpmk {
+
+constexpr int kThreads = 256;   // CTA size for every kernel of the path
+constexpr int kWarps = kThreads / 32;
+
+// device error codes (match the negative BPM_ERR_* values of bpm.h)
+constexpr int kDevErrTimeout = -4;
+constexpr int kDevErrNan = -5;
+
+// What a half-step launch does: rows (forward transform of the entrance
+// field; one propagation step's row half; the last slice's; inverse transform
+// accumulated into an output) or columns (propagator; focusing filter of the
+// multiplexed synthesis).
+enum RowMode { ROW_FWD = 0, ROW_STEP = 1, ROW_LAST = 2, ROW_INV_ACC = 3 };
+enum ColMode { COL_PROP = 0, COL_FOCUS = 1 };
+
+// Everything one propagation (or synthesis) launch needs.  The field is
+// [ny][nx] row-major: rows have length nx, columns length ny.
+struct StepArgs {
+  float2* work;            // [ny][nx] working field; holds E_out at the end
+  const float2* ein;       // [ny][nx] input field (read once)
+  const __half* dn;        // [nz][ny][nx] index volume (dn = n - n0)
+  float* inten;            // [iz1 - iz0][ny][nx] or nullptr
+  int iz0, iz1;            // intensity window: slice z in [iz0, iz1) goes to inten[z - iz0]
+  int nx, ny;              // grid (row length, column length)
+  // per-half-step launches of a grid whose row and column transforms differ
+  // in kind (rolled loop or not): the column kernel conjugates its output
+  // so that the row kernel receives the hand-off it expects
+  int flip_col;
+  // locally adapted expansion (reading B), nullptr when off: the mean index
+  // step of each slice and G = k0^2 n0 dz / kz0 per component, transposed
+  // like ht; slice z's propagator is H exp(i delta[z] G), its screen acts on
+  // dn - delta[z]
+  const float* delta;
+  const float* gt;
+  // propagation towards -z: loop step z handles slice z_begin + z_end - 1 - z
+  // (index, slice mean and intensity of that slice); the field enters at the
+  // exit plane of slice z_end - 1
+  int reverse;
+  // complex index (absorption): imaginary part kappa of n per voxel,
+  // [nz][ny][nx] FP16, or nullptr; the screen attenuates by exp(-k0 kappa dz)
+  const __half* kappa;
+  const float2* ht;        // [nx][ny] propagator, transposed: ht[kx * ny + ky]
+  const float2* tw;        // twiddles of the launch's transforms (row tables, then column tables)
+  float screen_c;          // k0 dz
+  float2 carrier;          // exp(i k0 n0 dz (z_end - z_begin))
+  int z_begin, z_end;
+  // focusing filter (synthesis): multiplier exp(-i kz zf) / (nx ny) inside the pupil
+  double k0n0, kna2, zf, dx, dy;   // k0 n0, (k0 NA)^2, focal depth, lateral spacings
+  double kin2;                     // (k0 NA_in)^2: inner edge of an annular pupil (0 for a disk)
+  int accumulate;                  // INV_ACC: add into out instead of storing
+  float2* out;                     // INV_ACC destination
+  // team barrier
+  unsigned* bar;
+  int* err;
+  unsigned long long timeout_ns;
+  unsigned bar_extra;
+  // persistent kernel: rows and columns per CTA at most, and which per-CTA
+  // buffers live in shared memory (propagator columns, index rows, intensity rows)
+  int rmax_r, rmax_c;
+  int h_res, dn_stage, i_stage;
+};
+
+// batched propagation (square grids): one instance's arguments
+struct InstArgs {
+  float2* work;
+  const float2* ein;
+  const __half* dn;
+  float* inten;
+  const float2* ht;
+  const float2* tw;
+  float screen_c;
+  float2 carrier;
+  int n, z_begin, z_end;
+  int iz0, iz1;             // intensity window (as in StepArgs)
+};
+
+struct BatchArgs {
+  const InstArgs* inst;         // [n_inst]
+  const int* order;             // queue order (instance indices, largest first)
+  int n_inst;
+  unsigned long long* queue;    // (taken from the front << 32) | taken from the back, zeroed before the launch
+  int* slots;                   // per-cluster broadcast of the fetched queue position
+  int slot_base;                // this launch's first slot (a fill launch follows the main one)
+  int from_back;                // 0: take from the front (largest first); 1: from the back (smallest first)
+  int back_min;                 // a back taker takes no position below this (too large for its team)
+  int* err;
+};
+
+// Position of the twiddle of butterfly b, radix element r, thread t within
+// one pass's table of a transform with T threads: [b][r][t], or with `paired`
+// (rolled-loop transforms, even R) [b][r/2][t][r%2] so that a thread reads
+// the twiddles of r and r + 1 with one 16-byte load.  The host and device
+// table builders both use it, so their layouts cannot drift apart.
+__host__ __device__ inline size_t twiddle_slot(int b, int r, int t, int R, int T, bool paired) {
+  return paired ? ((size_t)(b * (R / 2) + r / 2) * T + t) * 2 + (r & 1) : (size_t)(b * R + r) * T + t;
+}
+
+}  // namespace bpmk

@@ -1,8 +1,8 @@
 // bpm_kernels.cuh - device side of the split-step beam-propagation library.
 //
-// A "team" of CTAs owns one field of N x N complex floats that lives in global
-// memory (L2-resident: 8 MiB at N = 1024).  Each slice of the method is two
-// half-steps separated by team-wide barriers:
+// A "team" of CTAs owns one field of ny rows x nx columns of complex floats
+// that lives in global memory (L2-resident: 8 MiB at 1024 x 1024).  Each slice
+// of the method is two half-steps separated by team-wide barriers:
 //
 //   column half-step  (CTA owns a block of columns):
 //       stage its columns in shared memory, FFT_y, multiply by the propagator
@@ -21,18 +21,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+#include "bpm_args.cuh"
 #include "fft.cuh"
 
 namespace bpmk {
 
-constexpr int kThreads = 256;   // CTA size for every kernel of the path
-constexpr int kWarps = kThreads / 32;
-
-// device error codes (match the negative BPM_ERR_* values of bpm.h)
-constexpr int kDevErrTimeout = -4;
-constexpr int kDevErrNan = -5;
-
-// Per-N transform configuration.  Two engines:
+// Per-length transform configuration.  Two engines:
 //  - LoopCfg: N = R^P with one radix R; a rolled pass loop (LoopFFT) and the
 //    inverse by conjugation, so a half-step is one compact loop over 2P passes
 //    with the pointwise operation (propagator or screen) in the middle.
@@ -42,17 +38,23 @@ constexpr int kDevErrNan = -5;
 // forward input / inverse output) and L(RL) (spectrum order, forward output /
 // inverse input), the shared-memory index map f, the group stride GS (chosen
 // so that FFT exchanges and column staging are free of bank conflicts for the
-// power-of-two sizes) and the twiddle table lengths.
+// power-of-two sizes) and the twiddle table lengths.  A group of T threads
+// holds one row or column; groups wider than a warp (T = 64) synchronise with
+// the named barrier 1 + group index.
 template <int N_, int T_, int GS_>
 struct CfgBase {
   static constexpr int N = N_, T = T_, GS = GS_;
   static constexpr int PTS = N_ / T_;
-  static constexpr int GPW = 32 / T_;
-  static constexpr int NG = kWarps * GPW;   // row/column groups per CTA
+  static constexpr int NG = kThreads / T_;   // row/column groups per CTA
+  static_assert(NG * T_ == kThreads, "groups must tile the CTA");
+  static_assert(T_ <= 32 || NG <= 15, "groups wider than a warp use named barriers 1..15");
   // four-step column transform (FourStepCfg): off by default
   static constexpr int FS_N1 = 0, FS_SA = 0, FS_SC = 0, TW4 = 0;
   static constexpr int BUFLEN = NG * GS_;   // float2 of the group / exchange buffers
   static constexpr int HS = N_;             // row stride of the staged propagator columns
+  __device__ __forceinline__ static int group() { return threadIdx.x / T_; }
+  __device__ __forceinline__ static int lane() { return threadIdx.x % T_; }
+  __device__ __forceinline__ static int bar(int gid) { return T_ > 32 ? 1 + gid : 0; }
 };
 
 template <int N_, int T_, int R_, int PAD_, int GS_>
@@ -63,16 +65,18 @@ struct LoopCfg : CfgBase<N_, T_, GS_> {
   static constexpr int TWF = E::TW, TWI = 0;
   static_assert(GS_ >= E::BUF, "group stride too small");
   __device__ __forceinline__ static int f(int i) { return E::f(i); }
-  __device__ __forceinline__ static void fwd(float2* v, float2* buf, const float2* twf, const float2*, int t) {
-    E::run_fwd(v, buf, twf, t);
+  __device__ __forceinline__ static void fwd(float2* v, float2* buf, const float2* twf, const float2*, int t,
+                                             int bar = 0) {
+    E::run_fwd(v, buf, twf, t, bar);
   }
-  __device__ __forceinline__ static void inv(float2* v, float2* buf, const float2* twf, const float2*, int t) {
-    E::run_inv(v, buf, twf, t);
+  __device__ __forceinline__ static void inv(float2* v, float2* buf, const float2* twf, const float2*, int t,
+                                             int bar = 0) {
+    E::run_inv(v, buf, twf, t, bar);
   }
   // inverse, mid(v) on natural-order data, forward: one rolled loop
   template <class Mid>
   __device__ __forceinline__ static void inv_mid_fwd(float2* v, float2* buf, const float2* twf,
-                                                     const float2*, int t, Mid&& mid) {
+                                                     const float2*, int t, Mid&& mid, int bar = 0) {
     conj_all(v, E::PTS);
 #pragma unroll 1
     for (int q = 0; q < 2 * E::NP; ++q) {
@@ -80,20 +84,20 @@ struct LoopCfg : CfgBase<N_, T_, GS_> {
         conj_all(v, E::PTS);
         mid(v);
       }
-      E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t);
+      E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t, bar);
     }
   }
   // forward, mid(v) on spectrum-order data, inverse: one rolled loop
   template <class Mid>
   __device__ __forceinline__ static void fwd_mid_inv(float2* v, float2* buf, const float2* twf,
-                                                     const float2*, int t, Mid&& mid) {
+                                                     const float2*, int t, Mid&& mid, int bar = 0) {
 #pragma unroll 1
     for (int q = 0; q < 2 * E::NP; ++q) {
       if (q == E::NP) {
         mid(v);
         conj_all(v, E::PTS);
       }
-      E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t);
+      E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t, bar);
     }
     conj_all(v, E::PTS);
   }
@@ -107,16 +111,17 @@ struct LoopCfg : CfgBase<N_, T_, GS_> {
   // for the forward transform.
   template <class Mid>
   __device__ __forceinline__ static void fwd_mid_fwd(float2* v, float2* buf, const float2* twf,
-                                                     const float2*, int t, Mid&& mid) {
+                                                     const float2*, int t, Mid&& mid, int bar = 0) {
 #pragma unroll 1
     for (int q = 0; q < 2 * E::NP; ++q) {
       if (q == E::NP) mid(v);
-      E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t);
+      E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t, bar);
     }
   }
   // conjugated data in, conjugate of the inverse out
-  __device__ __forceinline__ static void inv_c(float2* v, float2* buf, const float2* twf, const float2*, int t) {
-    E::run_fwd(v, buf, twf, t);
+  __device__ __forceinline__ static void inv_c(float2* v, float2* buf, const float2* twf, const float2*, int t,
+                                               int bar = 0) {
+    E::run_fwd(v, buf, twf, t, bar);
   }
 };
 
@@ -130,25 +135,27 @@ struct GroupCfg : CfgBase<N_, T_, GS_> {
   static_assert(GS_ >= F::BUF && GS_ >= I::BUF, "group stride too small");
   static_assert(F::RL == I::R0 && I::RL == F::R0, "inverse must reverse the radices");
   __device__ __forceinline__ static int f(int i) { return F::f(i); }
-  __device__ __forceinline__ static void fwd(float2* v, float2* buf, const float2* twf, const float2*, int t) {
-    F::run(v, buf, twf, t);
+  __device__ __forceinline__ static void fwd(float2* v, float2* buf, const float2* twf, const float2*, int t,
+                                             int bar = 0) {
+    F::run(v, buf, twf, t, bar);
   }
-  __device__ __forceinline__ static void inv(float2* v, float2* buf, const float2*, const float2* twi, int t) {
-    I::run(v, buf, twi, t);
+  __device__ __forceinline__ static void inv(float2* v, float2* buf, const float2*, const float2* twi, int t,
+                                             int bar = 0) {
+    I::run(v, buf, twi, t, bar);
   }
   template <class Mid>
   __device__ __forceinline__ static void inv_mid_fwd(float2* v, float2* buf, const float2* twf,
-                                                     const float2* twi, int t, Mid&& mid) {
-    I::run(v, buf, twi, t);
+                                                     const float2* twi, int t, Mid&& mid, int bar = 0) {
+    I::run(v, buf, twi, t, bar);
     mid(v);
-    F::run(v, buf, twf, t);
+    F::run(v, buf, twf, t, bar);
   }
   template <class Mid>
   __device__ __forceinline__ static void fwd_mid_inv(float2* v, float2* buf, const float2* twf,
-                                                     const float2* twi, int t, Mid&& mid) {
-    F::run(v, buf, twf, t);
+                                                     const float2* twi, int t, Mid&& mid, int bar = 0) {
+    F::run(v, buf, twf, t, bar);
     mid(v);
-    I::run(v, buf, twi, t);
+    I::run(v, buf, twi, t, bar);
   }
 };
 
@@ -188,12 +195,13 @@ using Rad6x8x8 = Radices<6, 8, 8>;
 using Rad8x8x4 = Radices<8, 8, 4>;
 using Rad4x8x8 = Radices<4, 8, 8>;
 
-// Cfg<N, S>: transform schedule S of size N (S = 0 the default; the other
-// schedules of a size are alternatives that bpm_autotune times for
-// single-field plans, kSchedules(N) of them).
+// Cfg<N, S>: transform schedule S of length N (S = 0 the default; the other
+// schedules of a length are alternatives that bpm_autotune times for
+// single-field square plans, kSchedules(N) of them).
 template <int N, int S = 0>
 struct Cfg;
 template <> struct Cfg<64> : LoopCfg<64, 8, 8, 8, 73> {};
+template <> struct Cfg<96> : GroupCfg<96, 8, 109, GroupFFT<96, 8, 8, -1, Radices<4, 4, 6>>, GroupFFT<96, 8, 8, +1, Radices<6, 4, 4>>> {};
 template <> struct Cfg<128> : GroupCfg<128, 8, 145, GroupFFT<128, 8, 8, -1, Rad8x16>, GroupFFT<128, 8, 16, +1, Rad16x8>> {};
 template <> struct Cfg<192> : GroupCfg<192, 8, 219, GroupFFT<192, 8, 8, -1, Rad8x8x3>, GroupFFT<192, 8, 8, +1, Rad3x8x8>> {};
 // 256 and 512: one row per warp (32 threads, 8 or 16 points each), so a
@@ -205,13 +213,18 @@ template <> struct Cfg<192> : GroupCfg<192, 8, 219, GroupFFT<192, 8, 8, -1, Rad8
 template <> struct Cfg<256> : GroupCfg<256, 32, 274, GroupFFT<256, 32, 16, -1, Rad8x8x4>, GroupFFT<256, 32, 16, +1, Rad4x8x8>> {};
 template <> struct Cfg<384> : GroupCfg<384, 16, 409, GroupFFT<384, 16, 16, -1, Rad8x8x6>, GroupFFT<384, 16, 16, +1, Rad6x8x8>> {};
 template <> struct Cfg<512> : LoopCfg<512, 32, 8, 16, 546> {};
+template <> struct Cfg<768> : GroupCfg<768, 32, 818, GroupFFT<768, 32, 16, -1, Radices<8, 8, 12>>, GroupFFT<768, 32, 16, +1, Radices<12, 8, 8>>> {};
 template <> struct Cfg<1024> : FourStepCfg<LoopCfg<1024, 32, 32, 32, 1058>, 32> {};
+// 1536 and 2048: two warps per row or column (64 threads, 24 or 32 points
+// each), synchronised by a named barrier per group
+template <> struct Cfg<1536> : GroupCfg<1536, 64, 1634, GroupFFT<1536, 64, 16, -1, Radices<8, 8, 24>>, GroupFFT<1536, 64, 16, +1, Radices<24, 8, 8>>> {};
+template <> struct Cfg<2048> : GroupCfg<2048, 64, 2178, GroupFFT<2048, 64, 16, -1, Radices<16, 16, 8>>, GroupFFT<2048, 64, 16, +1, Radices<8, 16, 16>>> {};
 
-// Alternative schedules (single-field plans; bpm_autotune keeps the fastest):
-// 512 as unrolled 8 x 8 x 8 or 16 x 16 x 2 passes with separate inverse
-// schedules, 256 with the pass order reversed or as the rolled radix-16 loop
-// on two rows per warp, 1024 with its columns staged through shared memory
-// like the rows instead of the four-step register layout.
+// Alternative schedules (single-field square plans; bpm_autotune keeps the
+// fastest): 512 as unrolled 8 x 8 x 8 or 16 x 16 x 2 passes with separate
+// inverse schedules, 256 with the pass order reversed or as the rolled
+// radix-16 loop on two rows per warp, 1024 with its columns staged through
+// shared memory like the rows instead of the four-step register layout.
 template <> struct Cfg<512, 1> : GroupCfg<512, 32, 546, GroupFFT<512, 32, 16, -1, Radices<8, 8, 8>>,
                                           GroupFFT<512, 32, 16, +1, Radices<8, 8, 8>>> {};
 template <> struct Cfg<512, 2> : GroupCfg<512, 32, 546, GroupFFT<512, 32, 16, -1, Radices<16, 16, 2>>,
@@ -220,15 +233,33 @@ template <> struct Cfg<256, 1> : GroupCfg<256, 32, 274, GroupFFT<256, 32, 16, -1
 template <> struct Cfg<256, 2> : LoopCfg<256, 16, 16, 16, 273> {};
 template <> struct Cfg<1024, 1> : LoopCfg<1024, 32, 32, 32, 1058> {};
 
-// number of schedules of size n (Cfg<n, 0> .. Cfg<n, kSchedules(n) - 1>)
+// number of schedules of length n (Cfg<n, 0> .. Cfg<n, kSchedules(n) - 1>)
 __host__ __device__ constexpr int kSchedules(int n) { return n == 256 || n == 512 ? 3 : (n == 1024 ? 2 : 1); }
 // schedule a single-field plan starts with: the fastest measured on a B300
 // (us per slice with the intensity volume: 256^2 6.80 / 6.82 / 8.84,
 // 512^2 10.91 / 10.28 / 9.86, 1024^2 14.15 / 16.14); batched plans always
-// use schedule 0, the one compiled into the batched kernel
+// use schedule 0, the one compiled into the batched kernel; the rows and
+// columns of a rectangular grid take the default of their own length
 __host__ __device__ constexpr int kDefaultSchedule(int n) { return n == 512 ? 2 : 0; }
 
-// shared memory of the half-step kernels: twiddle tables, then the buffers
+// One grid's transforms: rows of length NX = CR::N (ny of them), columns of
+// length NY = CC::N (nx of them).  Shared memory of the persistent kernel
+// holds the row tables (forward, inverse), then the column tables (forward,
+// inverse, four-step); a square grid whose rows and columns share one
+// configuration keeps one copy.
+template <class CR_, class CC_>
+struct Pair {
+  using CR = CR_;
+  using CC = CC_;
+  static constexpr int NX = CR::N, NY = CC::N;
+  static constexpr bool kSame = std::is_same<CR_, CC_>::value;
+  static constexpr int TW_ROW = CR::TWF + CR::TWI;
+  static constexpr int TW_COL_OFF = kSame ? 0 : TW_ROW;   // column tables (forward, inverse, four-step)
+  static constexpr int TW_TOTAL = kSame ? CR::TWF + CR::TWI + CR::TW4 : TW_ROW + CC::TWF + CC::TWI + CC::TW4;
+  static constexpr int BUFLEN = CR::BUFLEN > CC::BUFLEN ? CR::BUFLEN : CC::BUFLEN;
+};
+
+// shared memory of the half-step kernels (one length): twiddle tables, then the buffers
 template <class C>
 __host__ __device__ constexpr size_t cfg_smem_bytes() {
   return sizeof(float2) * (size_t)(C::TWF + C::TWI + C::TW4 + C::BUFLEN);
@@ -237,7 +268,11 @@ template <class C>
 __host__ __device__ constexpr int cfg_twiddles() {
   return C::TWF + C::TWI + C::TW4;
 }
-
+// ... and of the persistent kernel of a grid, before its staging buffers
+template <class P>
+__host__ __device__ constexpr size_t pair_smem_bytes() {
+  return sizeof(float2) * (size_t)(P::TW_TOTAL + P::BUFLEN);
+}
 // exp(i x) for the phase screen: the Taylor series of sin and cos evaluated
 // by Horner's rule in x^2 (branch free), for |x| <= pi/4 truncated after x^11
 // and x^12 (truncation below 1e-11), with a shorter form for |x| <= 1/8
@@ -334,47 +369,6 @@ __device__ __forceinline__ int phasor_range(float max_abs_phase) {
   if (__all_sync(0xffffffffu, !(max_abs_phase > kPhasorTinyMax))) return 0;
   return __all_sync(0xffffffffu, !(max_abs_phase > kPhasorPolyMax)) ? 1 : 2;
 }
-
-// Everything one propagation (or synthesis) launch needs.
-struct StepArgs {
-  float2* work;            // [n][n] working field; holds E_out at the end
-  const float2* ein;       // [n][n] input field (read once)
-  const __half* dn;        // [nz][n][n] index volume (dn = n - n0)
-  float* inten;            // [iz1 - iz0][n][n] or nullptr
-  int iz0, iz1;            // intensity window: slice z in [iz0, iz1) goes to inten[z - iz0]
-  // locally adapted expansion (reading B), nullptr when off: the mean index
-  // step of each slice and G = k0^2 n0 dz / kz0 per component, transposed
-  // like ht; slice z's propagator is H exp(i delta[z] G), its screen acts on
-  // dn - delta[z]
-  const float* delta;
-  const float* gt;
-  // propagation towards -z: loop step z handles slice z_begin + z_end - 1 - z
-  // (index, slice mean and intensity of that slice); the field enters at the
-  // exit plane of slice z_end - 1
-  int reverse;
-  // complex index (absorption): imaginary part kappa of n per voxel,
-  // [nz][n][n] FP16, or nullptr; the screen attenuates by exp(-k0 kappa dz)
-  const __half* kappa;
-  const float2* ht;        // [n][n] propagator, transposed: ht[kx * n + ky]
-  const float2* tw;        // twiddles: forward table then inverse table
-  float screen_c;          // k0 dz
-  float2 carrier;          // exp(i k0 n0 dz (z_end - z_begin))
-  int z_begin, z_end;
-  // focusing filter (synthesis): multiplier exp(-i kz zf) / (n n) inside the pupil
-  double k0n0, kna2, zf, dx, dy;   // k0 n0, (k0 NA)^2, focal depth, lateral spacings
-  double kin2;                     // (k0 NA_in)^2: inner edge of an annular pupil (0 for a disk)
-  int accumulate;                  // INV_ACC: add into out instead of storing
-  float2* out;                     // INV_ACC destination
-  // team barrier
-  unsigned* bar;
-  int* err;
-  unsigned long long timeout_ns;
-  unsigned bar_extra;
-  // persistent kernel: rows (= columns) per CTA at most, and which per-CTA
-  // buffers live in shared memory (propagator columns, index rows, intensity rows)
-  int rmax;
-  int h_res, dn_stage, i_stage;
-};
 
 // Per-CTA shared-memory copies used by the half-steps (nullptr = use global).
 struct Stage {
@@ -505,8 +499,6 @@ __device__ __forceinline__ void adapt_multiply(float2* w, float dl, GK&& gk) {
 // ---------------------------------------------------------------------------
 // half-steps
 // ---------------------------------------------------------------------------
-enum RowMode { ROW_FWD = 0, ROW_STEP = 1, ROW_LAST = 2, ROW_INV_ACC = 3 };
-enum ColMode { COL_PROP = 0, COL_FOCUS = 1 };
 
 // Loads in the order the first radix-R pass consumes them, stores in the
 // order the last one produces them (dft_input_order / dft_output_order).
@@ -527,17 +519,19 @@ __device__ __forceinline__ void store_layout(const float2* v, float2* dst, int t
   }
 }
 
-// Rows [r0, r1) of the team member; each group of T threads takes one row per
-// round.  Groups without a row run the transforms on zeros (so that the warp
-// stays converged for __syncwarp) and skip all memory traffic.
-template <int N, int MODE, bool KAPPA = false, bool PK = true, int S = 0>
+// Rows [r0, r1) of the team member (rows of length C::N; NYc rows in all, or
+// a.ny when NYc is 0); each group of T threads takes one row per round.
+// Groups without a row run the transforms on zeros (so that the warp or
+// group stays converged for its barriers) and skip all memory traffic.
+template <class C, int NYc, int MODE, bool KAPPA = false, bool PK = true>
 __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1, int z, float2* s_buf,
                                               const float2* s_twf, const float2* s_twi, bool& bad,
                                               const Stage& st = Stage()) {
-  using C = Cfg<N, S>;
-  const int lane = threadIdx.x & 31;
-  const int gid = (threadIdx.x >> 5) * C::GPW + lane / C::T;
-  const int t = lane % C::T;
+  constexpr int N = C::N;
+  const int ny = NYc ? NYc : a.ny;
+  const int gid = C::group();
+  const int t = C::lane();
+  const int gbar = C::bar(gid);
   float2* buf = s_buf + gid * C::GS;
   const int rounds = (r1 - r0 + C::NG - 1) / C::NG;
   for (int k = 0; k < rounds; ++k) {
@@ -549,14 +543,14 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
       else
 #pragma unroll
         for (int q = 0; q < C::PTS; ++q) v[q] = make_float2(0.f, 0.f);
-      C::fwd(v, buf, s_twf, s_twi, t);
+      C::fwd(v, buf, s_twf, s_twi, t, gbar);
       if (active) store_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
     } else if constexpr (MODE == ROW_INV_ACC) {
       if (active) load_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
       else
 #pragma unroll
         for (int q = 0; q < C::PTS; ++q) v[q] = make_float2(0.f, 0.f);
-      C::inv(v, buf, s_twf, s_twi, t);
+      C::inv(v, buf, s_twf, s_twi, t, gbar);
       if (active) {
         float2* dst = a.out + (size_t)row * N;
 #pragma unroll
@@ -577,7 +571,7 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
       // inverse transform so that their latency hides behind it
       __half dv[C::PTS];
       if (!st.dn) {
-        const __half* dnrow = a.dn + ((size_t)z * N + (active ? row : r0)) * N;
+        const __half* dnrow = a.dn + ((size_t)z * ny + (active ? row : r0)) * N;
 #pragma unroll
         for (int q = 0; q < C::PTS; ++q) dv[q] = __ldcs(dnrow + layout_index<N, C::T, C::R0>(q, t));
       }
@@ -587,10 +581,10 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
       // rows would move the persistent kernel to the next, larger
       // shared-memory carve-out and shrink L1, which slows the lossless path
       const __half* skap = nullptr;
-      if constexpr (KAPPA) skap = a.kappa + ((size_t)z * N + (active ? row : r0)) * N;
+      if constexpr (KAPPA) skap = a.kappa + ((size_t)z * ny + (active ? row : r0)) * N;
       float* irow = nullptr;
       if (active && a.inten && z >= a.iz0 && z < a.iz1)
-        irow = st.inten ? st.inten + (size_t)(row - r0) * N : a.inten + ((size_t)(z - a.iz0) * N + row) * N;
+        irow = st.inten ? st.inten + (size_t)(row - r0) * N : a.inten + ((size_t)(z - a.iz0) * ny + row) * N;
       const bool i_smem = st.inten != nullptr;
       // LoopFFT sizes receive the conjugated spectrum from the column
       // half-step (LoopCfg::fwd_mid_fwd): the screen multiplies conj(w)
@@ -684,8 +678,8 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
         }
       };
       if constexpr (MODE == ROW_LAST) {
-        if constexpr (CJ) C::inv_c(v, buf, s_twf, s_twi, t);
-        else C::inv(v, buf, s_twf, s_twi, t);
+        if constexpr (CJ) C::inv_c(v, buf, s_twf, s_twi, t, gbar);
+        else C::inv(v, buf, s_twf, s_twi, t, gbar);
         screen(v);
         if (active) {
 #pragma unroll
@@ -693,8 +687,8 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
           store_layout<N, C::T, C::R0>(v, a.work + (size_t)row * N, t);
         }
       } else {
-        if constexpr (CJ) C::fwd_mid_fwd(v, buf, s_twf, s_twi, t, screen);
-        else C::inv_mid_fwd(v, buf, s_twf, s_twi, t, screen);
+        if constexpr (CJ) C::fwd_mid_fwd(v, buf, s_twf, s_twi, t, screen, gbar);
+        else C::inv_mid_fwd(v, buf, s_twf, s_twi, t, screen, gbar);
         if (active) store_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
       }
     }
@@ -726,14 +720,16 @@ __device__ __forceinline__ void four_step_fwd(float2* v, const float4* tw, float
   Dft<N1, -1>::run(v);
 }
 
-// Columns [c0, c1) by four-step transforms (FourStepCfg): load, FFT_y,
-// propagator H^T[col][ky], inverse FFT_y (conjugated forward), store, NG
-// columns per round, all in registers apart from the two exchanges.
-template <int N, int S = 0>
+// Columns [c0, c1) (length C::N; row stride NXc, or a.nx when NXc is 0) by
+// four-step transforms (FourStepCfg): load, FFT_y, propagator H^T[col][ky],
+// inverse FFT_y (conjugated forward), store, NG columns per round, all in
+// registers apart from the two exchanges.
+template <class C, int NXc, int FLIP>
 __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int c1, int z, float2* s_buf,
                                                  const float2* s_tw4, const Stage& st) {
-  using C = Cfg<N, S>;
+  constexpr int N = C::N;
   constexpr int N1 = C::FS_N1, NG = C::NG, SA = C::FS_SA, SC = C::FS_SC;
+  const int nx = NXc ? NXc : a.nx;
   const int c = threadIdx.x % NG, ai = threadIdx.x / NG;
   // [k/2][a][k%2] pairs (16-byte aligned: the table follows whole tables)
   const float4* tw = reinterpret_cast<const float4*>(s_tw4) + ai;
@@ -748,7 +744,7 @@ __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int 
 #pragma unroll
       for (int i = 0; i < N1; ++i) {
         const int b = dft_input_order<N1>(i);
-        v[b] = __ldcg(src + (size_t)(ai + N1 * b) * N);
+        v[b] = __ldcg(src + (size_t)(ai + N1 * b) * nx);
       }
     }
     four_step_fwd<N1, SA>(v, tw, xw, xr);
@@ -768,33 +764,40 @@ __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int 
       adapt_multiply<N1>(v, -a.delta[z], [&](int k) { return __ldg(g + N1 * k); });
     }
     four_step_fwd<N1, SA>(v, tw, xw, xr);
+    if (FLIP == 1 || (FLIP == 2 && a.flip_col)) conj_all(v, N1);
     if (on) {
       float2* dst = a.work + col;
 #pragma unroll
       for (int i = 0; i < N1; ++i) {
         const int b = dft_output_order<N1>(i);
-        __stcg(dst + (size_t)(ai + N1 * b) * N, v[b]);
+        __stcg(dst + (size_t)(ai + N1 * b) * nx, v[b]);
       }
     }
   }
 }
 
-// Columns [c0, c1) of the team member, NG columns per round staged in shared
-// memory (column g of the round at s_buf + g * GS, index padded like the
-// forward transform's exchange buffer).  Sizes with a four-step layout take
-// col_half_step_4s for the propagator.
-template <int N, int MODE, int S = 0>
+// Columns [c0, c1) of the team member (length C::N, row stride NXc or a.nx),
+// NG columns per round staged in shared memory (column g of the round at
+// s_buf + g * GS, index padded like the forward transform's exchange buffer).
+// Lengths with a four-step layout take col_half_step_4s for the propagator.
+// The propagator step hands the rows conjugated data when the column
+// configuration is a rolled loop (LoopCfg::fwd_mid_fwd), and the row
+// half-step expects conjugated data when the row configuration is one; when
+// the two differ (a rectangular grid) FLIP conjugates the columns' output
+// (FLIP 1: always; 2: when a.flip_col is set, for the per-half-step launches).
+template <class C, int NXc, int MODE, int FLIP = 0>
 __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1, int z, float2* s_buf,
                                               const float2* s_twf, const float2* s_twi,
                                               const Stage& st = Stage()) {
-  using C = Cfg<N, S>;
+  constexpr int N = C::N;
   if constexpr (C::FS_N1 > 0 && MODE == COL_PROP) {
-    col_half_step_4s<N, S>(a, c0, c1, z, s_buf, s_twi + C::TWI, st);
+    col_half_step_4s<C, NXc, FLIP>(a, c0, c1, z, s_buf, s_twi + C::TWI, st);
     return;
   }
-  const int lane = threadIdx.x & 31;
-  const int gid = (threadIdx.x >> 5) * C::GPW + lane / C::T;
-  const int t = lane % C::T;
+  const int nx = NXc ? NXc : a.nx;
+  const int gid = C::group();
+  const int t = C::lane();
+  const int gbar = C::bar(gid);
   float2* buf = s_buf + gid * C::GS;
   static_assert(kThreads % C::NG == 0, "");
   constexpr int YSTEP = kThreads / C::NG;
@@ -815,7 +818,7 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
         float2 tmp[CHUNK];
 #pragma unroll
         for (int i = 0; i < CHUNK; ++i)
-          tmp[i] = on ? __ldcg(src + (size_t)(y0 + (c + i) * YSTEP) * N) : make_float2(0.f, 0.f);
+          tmp[i] = on ? __ldcg(src + (size_t)(y0 + (c + i) * YSTEP) * nx) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < CHUNK; ++i) s_buf[cc * C::GS + C::f(y0 + (c + i) * YSTEP)] = tmp[i];
       }
@@ -827,7 +830,7 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
 #pragma unroll
     for (int q = 0; q < C::PTS; ++q)
       v[q] = active ? buf[C::f(layout_index<N, C::T, C::R0>(q, t))] : make_float2(0.f, 0.f);
-    __syncwarp();
+    group_sync<C::T>(gbar);
     if constexpr (MODE == COL_PROP) {
       const float2* hcol = st.h ? st.h + (size_t)((active ? col : c0) - c0) * C::HS
                                 : a.ht + (size_t)(active ? col : c0) * N;
@@ -849,13 +852,14 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
                                  [&](int q) { return __ldg(g + layout_index<N, C::T, C::RL>(q, t)); });
         }
       };
-      if constexpr (CJ) C::fwd_mid_fwd(v, buf, s_twf, s_twi, t, prop);
-      else C::fwd_mid_inv(v, buf, s_twf, s_twi, t, prop);
+      if constexpr (CJ) C::fwd_mid_fwd(v, buf, s_twf, s_twi, t, prop, gbar);
+      else C::fwd_mid_inv(v, buf, s_twf, s_twi, t, prop, gbar);
+      if (FLIP == 1 || (FLIP == 2 && a.flip_col)) conj_all(v, C::PTS);
     } else {
-      // focusing filter: exp(-i kz zf) / (n n) inside the pupil, 0 outside;
+      // focusing filter: exp(-i kz zf) / (nx ny) inside the pupil, 0 outside;
       // membership decided in FP64 with the same operation order as the oracle
-      const int fx = col < (N + 1) / 2 ? col : col - N;
-      const double kx = __ddiv_rn(__dmul_rn(6.283185307179586, (double)fx), __dmul_rn((double)N, a.dx));
+      const int fx = col < (nx + 1) / 2 ? col : col - nx;
+      const double kx = __ddiv_rn(__dmul_rn(6.283185307179586, (double)fx), __dmul_rn((double)nx, a.dx));
       const double ndy = __dmul_rn((double)N, a.dy);
       C::fwd_mid_inv(v, buf, s_twf, s_twi, t, [&](float2* w) {
 #pragma unroll
@@ -871,12 +875,12 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
             ph -= 6.283185307179586 * rint(ph * 0.15915494309189535);
             float sn, cs;
             sincosf((float)ph, &sn, &cs);
-            const float sc = 1.0f / ((float)N * (float)N);
+            const float sc = 1.0f / ((float)nx * (float)N);
             m = make_float2(cs * sc, sn * sc);
           }
           w[q] = cmul(w[q], m);
         }
-      });
+      }, gbar);
     }
     if (active) {
 #pragma unroll
@@ -890,18 +894,16 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
 #pragma unroll 8
         for (int i = 0; i < PER; ++i) {
           const int y = y0 + i * YSTEP;
-          __stcg(dst + (size_t)y * N, s_buf[cc * C::GS + C::f(y)]);
+          __stcg(dst + (size_t)y * nx, s_buf[cc * C::GS + C::f(y)]);
         }
       }
     }
   }
 }
 
-template <int N, int S = 0>
-__device__ __forceinline__ void load_twiddles(const StepArgs& a, float2* s_twf, float2* s_twi) {
-  // the tables are contiguous: forward, inverse, four-step
-  (void)s_twi;
-  for (int i = threadIdx.x; i < cfg_twiddles<Cfg<N, S>>(); i += kThreads) s_twf[i] = __ldg(a.tw + i);
+// count twiddles from global to shared memory (ends with __syncthreads)
+__device__ __forceinline__ void load_twiddles(const float2* src, float2* dst, int count) {
+  for (int i = threadIdx.x; i < count; i += kThreads) dst[i] = __ldg(src + i);
   __syncthreads();
 }
 
@@ -913,118 +915,76 @@ __device__ __forceinline__ void report_bad(const StepArgs& a, bool bad) {
 // kernels
 // ---------------------------------------------------------------------------
 
-// Mean index step of every slice (reading B): CTA z sums slice z0 + z of the
-// FP16 volume (FP32 partial sums of at most M / kThreads values per thread,
-// FP64 across the block) into delta[z].
-__global__ void __launch_bounds__(kThreads) bpm_slice_mean_kernel(const __half* __restrict__ dn, size_t M,
-                                                                  float* __restrict__ delta) {
-  const __half* slice = dn + (size_t)blockIdx.x * M;
-  float acc = 0.f;
-  const size_t M8 = M / 8;   // 16-byte loads of 8 values (M is a multiple of 8)
-  for (size_t i = threadIdx.x; i < M8; i += kThreads) {
-    const uint4 u = __ldcs(reinterpret_cast<const uint4*>(slice) + i);
-    const __half2* h = reinterpret_cast<const __half2*>(&u);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float2 f = __half22float2(h[k]);
-      acc += f.x + f.y;
-    }
-  }
-  for (size_t i = M8 * 8 + threadIdx.x; i < M; i += kThreads) acc += __half2float(slice[i]);
-  __shared__ double part[kWarps];
-  double d = acc;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = d;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kWarps; ++w) t += part[w];
-    delta[blockIdx.x] = (float)(t / (double)M);
-  }
-}
-
-// G = k0^2 n0 dz / kz0 per component (0 where the propagator is cut), laid out
-// like ht ([kx][ky]); the cut is decided exactly as in bpm_build_ht_kernel.
-__global__ void bpm_build_gt_kernel(float* gt, int nx, int ny, double dx, double dy, double dz, double lambda,
-                                    double n0) {
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i >= (size_t)nx * ny) return;
-  const int kyi = (int)(i % ny), kxi = (int)(i / ny);
-  const int fx = kxi < (nx + 1) / 2 ? kxi : kxi - nx;
-  const int fy = kyi < (ny + 1) / 2 ? kyi : kyi - ny;
-  const double twopi = 6.283185307179586;
-  const double k0 = __ddiv_rn(twopi, lambda);
-  const double K = __dmul_rn(k0, n0);
-  const double kx = __ddiv_rn(__dmul_rn(twopi, (double)fx), __dmul_rn((double)nx, dx));
-  const double ky = __ddiv_rn(__dmul_rn(twopi, (double)fy), __dmul_rn((double)ny, dy));
-  const double kz2 = __dsub_rn(__dsub_rn(__dmul_rn(K, K), __dmul_rn(kx, kx)), __dmul_rn(ky, ky));
-  gt[i] = kz2 > 0.0 ? (float)(k0 * k0 * n0 * dz / sqrt(kz2)) : 0.f;
-}
-
 // The whole slice loop in one cooperative launch; gridDim.x CTAs form the team
 // (rows split evenly, columns in aligned groups of NG).
-// Shared memory: twiddles | group buffers | [propagator columns of this CTA]
-// | [index rows of the current slice] | [intensity rows of the current slice].
-// The index rows of slice z are fetched by one bulk copy issued when the
-// column half-step of slice z starts, so the HBM read overlaps it; the
-// intensity rows are written to shared memory by the row half-step and sent
-// to HBM by one bulk store that overlaps the next column half-step.
-template <int N, bool KAPPA = false, int S = 0>
+// Shared memory: twiddles (rows, columns) | group buffers | [propagator
+// columns of this CTA] | [index rows of the current slice] | [intensity rows
+// of the current slice].  The index rows of slice z are fetched by one bulk
+// copy issued when the column half-step of slice z starts, so the HBM read
+// overlaps it; the intensity rows are written to shared memory by the row
+// half-step and sent to HBM by one bulk store that overlaps the next column
+// half-step.
+template <class P, bool KAPPA = false>
 __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a) {
-  using C = Cfg<N, S>;
+  using CR = typename P::CR;
+  using CC = typename P::CC;
+  constexpr int NX = P::NX, NY = P::NY;
   extern __shared__ float4 smem_f4[];
-  float2* s_twf = reinterpret_cast<float2*>(smem_f4);
-  float2* s_twi = s_twf + C::TWF;
-  float2* s_buf = s_twi + C::TWI + C::TW4;
-  char* s_extra = reinterpret_cast<char*>(s_buf + C::BUFLEN);
+  float2* s_tw = reinterpret_cast<float2*>(smem_f4);
+  const float2* s_twr_f = s_tw;                           // row tables
+  const float2* s_twr_i = s_tw + CR::TWF;
+  const float2* s_twc_f = s_tw + P::TW_COL_OFF;           // column tables
+  const float2* s_twc_i = s_twc_f + CC::TWF;
+  float2* s_buf = s_tw + P::TW_TOTAL;
+  char* s_extra = reinterpret_cast<char*>(s_buf + P::BUFLEN);
   __shared__ int s_flag;
   __shared__ __align__(8) uint64_t s_mbar;
   const int G = gridDim.x, rank = blockIdx.x;
-  const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
+  const int lo = (int)(((long long)rank * NY) / G), hi = (int)(((long long)(rank + 1) * NY) / G);
   const int nrow = hi - lo;
-  // columns in whole groups of NG (aligned 64-byte segments at N = 1024): a
-  // team larger than N / NG leaves its last CTAs without columns, while every
-  // CTA still takes rows
-  const int cper = (N + G - 1) / G, CB = (cper + C::NG - 1) / C::NG * C::NG;
-  const int clo = min(N, rank * CB), chi = min(N, clo + CB);
+  // columns in whole groups of NG (aligned 64-byte segments at 1024 x 1024):
+  // a team larger than NX / NG leaves its last CTAs without columns, while
+  // every CTA still takes rows
+  const int cper = (NX + G - 1) / G, CB = (cper + CC::NG - 1) / CC::NG * CC::NG;
+  const int clo = min(NX, rank * CB), chi = min(NX, clo + CB);
   Stage st;
   {
     size_t off = 0;
     if (a.h_res) {
       st.h = reinterpret_cast<const float2*>(s_extra + off);
-      off += ((size_t)a.rmax * C::HS * sizeof(float2) + 15) & ~(size_t)15;
+      off += ((size_t)a.rmax_c * CC::HS * sizeof(float2) + 15) & ~(size_t)15;
     }
     if (a.dn_stage) {
       st.dn = reinterpret_cast<const __half*>(s_extra + off);
-      off += ((size_t)a.rmax * N * sizeof(__half) + 15) & ~(size_t)15;
+      off += ((size_t)a.rmax_r * NX * sizeof(__half) + 15) & ~(size_t)15;
     }
 
     if (a.i_stage && a.inten) st.inten = reinterpret_cast<float*>(s_extra + off);
   }
   if (a.h_res) {
     float2* dst = const_cast<float2*>(st.h);
-    const float2* src = a.ht + (size_t)clo * N;
-    for (int i = threadIdx.x; i < (chi - clo) * N; i += kThreads) dst[(i / N) * C::HS + i % N] = __ldg(src + i);
+    const float2* src = a.ht + (size_t)clo * NY;
+    for (int i = threadIdx.x; i < (chi - clo) * NY; i += kThreads) dst[(i / NY) * CC::HS + i % NY] = __ldg(src + i);
   }
   if (threadIdx.x == 0 && a.dn_stage) mbar_init(&s_mbar, 1);
-  load_twiddles<N, S>(a, s_twf, s_twi);    // ends with __syncthreads
+  load_twiddles(a.tw, s_tw, P::TW_TOTAL);    // ends with __syncthreads
   unsigned epoch = 0, dn_parity = 0;
   bool bad = false, dn_pending = false;
-  row_half_step<N, ROW_FWD, false, true, S>(a, lo, hi, a.z_begin, s_buf, s_twf, s_twi, bad);
+  row_half_step<CR, NY, ROW_FWD>(a, lo, hi, a.z_begin, s_buf, s_twr_f, s_twr_i, bad);
   if (!team_barrier(a, epoch, &s_flag)) return;
   for (int zi = a.z_begin; zi < a.z_end; ++zi) {
     const bool last = zi + 1 == a.z_end;
     const int z = a.reverse ? a.z_begin + a.z_end - 1 - zi : zi;     // the slice this step crosses
     if (a.dn_stage && nrow > 0) {
       if (threadIdx.x == 0) {
-        const unsigned bytes = (unsigned)((size_t)nrow * N * sizeof(__half));
+        const unsigned bytes = (unsigned)((size_t)nrow * NX * sizeof(__half));
         mbar_arrive_expect_tx(&s_mbar, bytes);
-        bulk_load(const_cast<__half*>(st.dn), a.dn + ((size_t)z * N + lo) * N, bytes, &s_mbar);
+        bulk_load(const_cast<__half*>(st.dn), a.dn + ((size_t)z * NY + lo) * NX, bytes, &s_mbar);
       }
       dn_pending = true;
     }
-    col_half_step<N, COL_PROP, S>(a, clo, chi, z, s_buf, s_twf, s_twi, st);
+    col_half_step<CC, NX, COL_PROP, (CC::kLoop != CR::kLoop ? 1 : 0)>(a, clo, chi, z, s_buf, s_twc_f, s_twc_i,
+                                                                        st);
     if (!team_barrier(a, epoch, &s_flag)) break;
     bool ok = true;
     if (dn_pending) {
@@ -1034,14 +994,14 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
     }
     if (st.inten && threadIdx.x == 0) bulk_wait_reads();   // previous intensity store has read its rows
     if (__syncthreads_or(!ok)) break;
-    if (!last) row_half_step<N, ROW_STEP, KAPPA, true, S>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
-    else row_half_step<N, ROW_LAST, KAPPA, true, S>(a, lo, hi, z, s_buf, s_twf, s_twi, bad, st);
+    if (!last) row_half_step<CR, NY, ROW_STEP, KAPPA>(a, lo, hi, z, s_buf, s_twr_f, s_twr_i, bad, st);
+    else row_half_step<CR, NY, ROW_LAST, KAPPA>(a, lo, hi, z, s_buf, s_twr_f, s_twr_i, bad, st);
     if (st.inten && z >= a.iz0 && z < a.iz1) {
       fence_proxy_async_smem();
       __syncthreads();
       if (threadIdx.x == 0 && nrow > 0)
-        bulk_store(a.inten + ((size_t)(z - a.iz0) * N + lo) * N, st.inten,
-                   (unsigned)((size_t)nrow * N * sizeof(float)));
+        bulk_store(a.inten + ((size_t)(z - a.iz0) * NY + lo) * NX, st.inten,
+                   (unsigned)((size_t)nrow * NX * sizeof(float)));
     }
     if (!last && !team_barrier(a, epoch, &s_flag)) break;
   }
@@ -1052,49 +1012,49 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
   report_bad(a, bad);
 }
 
-// One half-step per launch (comparison path and input synthesis).
-template <int N, int MODE, bool KAPPA = false, int S = 0>
+// One half-step per launch (comparison path and input synthesis): rows of
+// length C::N (a.ny of them), or columns of length C::N (a.nx of them).
+// Shared memory: the length's tables (forward, inverse, four-step) | buffers.
+template <class C, int MODE, bool KAPPA = false>
 __global__ void __launch_bounds__(kThreads, 1) bpm_row_kernel(StepArgs a, int z) {
-  using C = Cfg<N, S>;
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
   float2* s_twi = s_twf + C::TWF;
   float2* s_buf = s_twi + C::TWI + C::TW4;
-  load_twiddles<N, S>(a, s_twf, s_twi);
+  load_twiddles(a.tw, s_twf, cfg_twiddles<C>());
   const int G = gridDim.x, rank = blockIdx.x;
-  const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
+  const int lo = (int)(((long long)rank * a.ny) / G), hi = (int)(((long long)(rank + 1) * a.ny) / G);
   bool bad = false;
-  row_half_step<N, MODE, KAPPA, true, S>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+  row_half_step<C, 0, MODE, KAPPA>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
   if constexpr (MODE == ROW_STEP || MODE == ROW_LAST) report_bad(a, bad);
 }
 
-template <int N, int MODE, int S = 0>
+template <class C, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) bpm_col_kernel(StepArgs a, int z) {
-  using C = Cfg<N, S>;
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
   float2* s_twi = s_twf + C::TWF;
   float2* s_buf = s_twi + C::TWI + C::TW4;
-  load_twiddles<N, S>(a, s_twf, s_twi);
+  load_twiddles(a.tw, s_twf, cfg_twiddles<C>());
   const int G = gridDim.x, rank = blockIdx.x;
-  const int lo = (int)(((long long)rank * N) / G), hi = (int)(((long long)(rank + 1) * N) / G);
-  col_half_step<N, MODE, S>(a, lo, hi, z, s_buf, s_twf, s_twi);
+  const int lo = (int)(((long long)rank * a.nx) / G), hi = (int)(((long long)(rank + 1) * a.nx) / G);
+  col_half_step<C, 0, MODE, 2>(a, lo, hi, z, s_buf, s_twf, s_twi);
 }
 
-// Light sheet: the ky = 0 spectrum line, inverse FFT_x by group 0 of warp 0,
-// then the row is copied to every y.  Every CTA computes the (short) line
-// itself and writes a share of the rows.  Dynamic shared memory: smem_bytes()
-// plus GS float2 for the spectrum line.
-template <int N, int S = 0>
+// Light sheet: the ky = 0 spectrum line (rows of length C::N), inverse FFT_x
+// by group 0, then the row is copied to every y.  Every CTA computes the
+// (short) line itself and writes a share of the rows.  Dynamic shared memory:
+// cfg_smem_bytes() plus GS float2 for the spectrum line.
+template <class C>
 __global__ void __launch_bounds__(kThreads, 1) bpm_light_sheet_kernel(StepArgs a, double w0, double xc) {
-  using C = Cfg<N, S>;
+  constexpr int N = C::N;
   extern __shared__ float4 smem_f4[];
   float2* s_twf = reinterpret_cast<float2*>(smem_f4);
   float2* s_twi = s_twf + C::TWF;
   float2* s_buf = s_twi + C::TWI + C::TW4;
   float2* line = s_buf + C::BUFLEN;
   __shared__ double s_part[kThreads];
-  load_twiddles<N, S>(a, s_twf, s_twi);
+  load_twiddles(a.tw, s_twf, cfg_twiddles<C>());
   const double nd = __dmul_rn((double)N, a.dx);
   // sum of A(kx) over propagating bins (FP64)
   double part = 0.0;
@@ -1131,90 +1091,32 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_light_sheet_kernel(StepArgs a
     line[C::f(x)] = sv;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int t = threadIdx.x % C::T;
-    const int g = threadIdx.x / C::T;
+  // the first warp (or the first group when a group spans several warps):
+  // all of its groups transform the line, group 0 writes it back
+  constexpr int LT = C::T > 32 ? C::T : 32;
+  if (threadIdx.x < LT) {
+    const int t = C::lane();
+    const int g = C::group();
     float2 v[C::PTS];
 #pragma unroll
     for (int q = 0; q < C::PTS; ++q) v[q] = line[C::f(layout_index<N, C::T, C::RL>(q, t))];
-    __syncwarp();
-    C::inv(v, s_buf + g * C::GS, s_twf, s_twi, t);
+    group_sync<C::T>(C::bar(g));
+    C::inv(v, s_buf + g * C::GS, s_twf, s_twi, t, C::bar(g));
     if (g == 0) {
 #pragma unroll
       for (int q = 0; q < C::PTS; ++q) line[C::f(layout_index<N, C::T, C::R0>(q, t))] = v[q];
     }
   }
   __syncthreads();
-  for (size_t i = blockIdx.x * (size_t)kThreads + threadIdx.x; i < (size_t)N * N;
+  for (size_t i = blockIdx.x * (size_t)kThreads + threadIdx.x; i < (size_t)N * a.ny;
        i += (size_t)gridDim.x * kThreads) {
     const int x = (int)(i % N);
     __stcg(a.work + i, line[C::f(x)]);
   }
 }
 
-// Scatter emitters: out[iy][ix] += amp exp(i phase).  One thread per emitter.
-__global__ void bpm_scatter_kernel(float2* field, int n, const int* idx, const double* phase, int count,
-                                   const unsigned long long* n_pupil) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= count) return;
-  const double np = (double)*n_pupil;
-  if (np <= 0.0) return;
-  const double amp = sqrt((double)n * (double)n / np);
-  double sn, cs;
-  sincos(phase[j], &sn, &cs);
-  float* p = reinterpret_cast<float*>(field + idx[j]);
-  atomicAdd(p, (float)(amp * cs));
-  atomicAdd(p + 1, (float)(amp * sn));
-}
-
-// Count DFT bins inside the pupil kin2 <= |k_perp|^2 <= kna2 that also propagate.
-__global__ void bpm_pupil_count_kernel(int n, double dx, double dy, double k0n0, double kin2, double kna2,
-                                       unsigned long long* count) {
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  unsigned long long c = 0;
-  if (i < (size_t)n * n) {
-    const int x = (int)(i % n), y = (int)(i / n);
-    const int fx = x < (n + 1) / 2 ? x : x - n, fy = y < (n + 1) / 2 ? y : y - n;
-    const double kx = __ddiv_rn(__dmul_rn(6.283185307179586, (double)fx), __dmul_rn((double)n, dx));
-    const double ky = __ddiv_rn(__dmul_rn(6.283185307179586, (double)fy), __dmul_rn((double)n, dy));
-    const double kp2 = __dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky));
-    const double kz2 = __dsub_rn(__dmul_rn(k0n0, k0n0), kp2);
-    c = (kp2 >= kin2 && kp2 <= kna2 && kz2 > 0.0) ? 1ull : 0ull;
-  }
-  // warp reduce, one atomic per warp
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
-}
-
-// Propagator table, transposed: ht[kx * ny + ky] = exp(i (kz - k0 n0) dz) / (nx ny)
-// for kz^2 = (k0 n0)^2 - kx^2 - ky^2 > 0, else 0.  FP64 throughout; the
-// cancellation-free form kz - k0 n0 = -k_perp^2 / (k0 n0 + kz) is used.
-__global__ void bpm_build_ht_kernel(float2* ht, int nx, int ny, double dx, double dy, double dz, double lambda,
-                                    double n0) {
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i >= (size_t)nx * ny) return;
-  const int kyi = (int)(i % ny), kxi = (int)(i / ny);
-  const int fx = kxi < (nx + 1) / 2 ? kxi : kxi - nx;
-  const int fy = kyi < (ny + 1) / 2 ? kyi : kyi - ny;
-  const double twopi = 6.283185307179586;
-  const double K = __dmul_rn(__ddiv_rn(twopi, lambda), n0);
-  const double kx = __ddiv_rn(__dmul_rn(twopi, (double)fx), __dmul_rn((double)nx, dx));
-  const double ky = __ddiv_rn(__dmul_rn(twopi, (double)fy), __dmul_rn((double)ny, dy));
-  const double kz2 = __dsub_rn(__dsub_rn(__dmul_rn(K, K), __dmul_rn(kx, kx)), __dmul_rn(ky, ky));
-  float2 h = make_float2(0.f, 0.f);
-  if (kz2 > 0.0) {
-    const double kp2 = kx * kx + ky * ky;
-    const double ph = -kp2 / (K + sqrt(kz2)) * dz;
-    double sn, cs;
-    sincos(ph, &sn, &cs);
-    const double sc = 1.0 / ((double)nx * (double)ny);
-    h = make_float2((float)(cs * sc), (float)(sn * sc));
-  }
-  ht[i] = h;
-}
-
 // ---------------------------------------------------------------------------
-// batched propagation: many independent instances, one persistent launch
+// batched propagation: many independent square instances, one persistent launch
 // ---------------------------------------------------------------------------
 // Every thread-block cluster is a team: it takes the next instance from a
 // device work queue (instances are queued largest first), runs all of that
@@ -1222,30 +1124,6 @@ __global__ void bpm_build_ht_kernel(float2* ht, int nx, int ny, double dx, doubl
 // (release/acquire at cluster scope, so the field exchanged through L2 is
 // visible), then takes the next one.  No grid-wide barrier is involved, so
 // clusters run independently and instances of different sizes mix freely.
-struct InstArgs {
-  float2* work;
-  const float2* ein;
-  const __half* dn;
-  float* inten;
-  const float2* ht;
-  const float2* tw;
-  float screen_c;
-  float2 carrier;
-  int n, z_begin, z_end;
-  int iz0, iz1;             // intensity window (as in StepArgs)
-};
-
-struct BatchArgs {
-  const InstArgs* inst;         // [n_inst]
-  const int* order;             // queue order (instance indices, largest first)
-  int n_inst;
-  unsigned long long* queue;    // (taken from the front << 32) | taken from the back, zeroed before the launch
-  int* slots;                   // per-cluster broadcast of the fetched queue position
-  int slot_base;                // this launch's first slot (a fill launch follows the main one)
-  int from_back;                // 0: take from the front (largest first); 1: from the back (smallest first)
-  int back_min;                 // a back taker takes no position below this (too large for its team)
-  int* err;
-};
 
 // One queue position for a team (its leader thread): the main launch takes
 // positions from the front of the order, a fill launch of smaller teams (on
@@ -1307,6 +1185,8 @@ __device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int
   a.inten = ia.inten;
   a.iz0 = ia.iz0;
   a.iz1 = ia.iz1;
+  a.nx = N;
+  a.ny = N;
   a.ht = ia.ht;
   a.tw = ia.tw;
   a.screen_c = ia.screen_c;
@@ -1324,77 +1204,15 @@ __device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int
     cluster_sync_all();
     return;
   }
-  load_twiddles<N>(a, s_twf, s_twi);
-  row_half_step<N, ROW_FWD>(a, lo, hi, a.z_begin, s_buf, s_twf, s_twi, bad);
+  load_twiddles(a.tw, s_twf, cfg_twiddles<C>());
+  row_half_step<C, N, ROW_FWD>(a, lo, hi, a.z_begin, s_buf, s_twf, s_twi, bad);
   cluster_sync_all();
   for (int z = a.z_begin; z < a.z_end; ++z) {
-    col_half_step<N, COL_PROP>(a, lo, hi, z, s_buf, s_twf, s_twi);
+    col_half_step<C, N, COL_PROP>(a, lo, hi, z, s_buf, s_twf, s_twi);
     cluster_sync_all();
-    if (z + 1 < a.z_end) row_half_step<N, ROW_STEP, false, false>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
-    else row_half_step<N, ROW_LAST, false, false>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+    if (z + 1 < a.z_end) row_half_step<C, N, ROW_STEP, false, false>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+    else row_half_step<C, N, ROW_LAST, false, false>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
     cluster_sync_all();
-  }
-}
-
-__global__ void __launch_bounds__(kThreads, 1) bpm_batch_kernel(BatchArgs b) {
-  extern __shared__ float4 smem_f4[];
-  float2* smem = reinterpret_cast<float2*>(smem_f4);
-  const int CL = (int)cluster_size(), rank = (int)cluster_rank(), cid = (int)cluster_id();
-  bool bad = false;
-  for (;;) {
-    if (rank == 0 && threadIdx.x == 0) b.slots[b.slot_base + cid] = batch_take(b);
-    cluster_sync_all();
-    const int k = ld_volatile(b.slots + b.slot_base + cid);
-    cluster_sync_all();     // every CTA has read the slot before the leader may overwrite it
-    if (k >= b.n_inst) break;
-    const InstArgs ia = b.inst[b.order[k]];
-    switch (ia.n) {
-      case 64: batch_instance<64>(ia, b.err, rank, CL, smem, bad); break;
-      case 128: batch_instance<128>(ia, b.err, rank, CL, smem, bad); break;
-      case 192: batch_instance<192>(ia, b.err, rank, CL, smem, bad); break;
-      case 256: batch_instance<256>(ia, b.err, rank, CL, smem, bad); break;
-      case 384: batch_instance<384>(ia, b.err, rank, CL, smem, bad); break;
-      case 512: batch_instance<512>(ia, b.err, rank, CL, smem, bad); break;
-      case 1024: batch_instance<1024>(ia, b.err, rank, CL, smem, bad); break;
-      default: break;
-    }
-  }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(b.err, 0, kDevErrNan);
-}
-
-// Phase conjugation of a field (time reversal of a monochromatic wave): E <- conj(E).
-__global__ void bpm_conj_kernel(float2* E, size_t M) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
-    float2 e = E[i];
-    e.y = -e.y;
-    E[i] = e;
-  }
-}
-
-// Per-focus patches of an intensity window (PSF de-multiplexing): thread i
-// of the grid-stride loop writes out[i], i = ((j pz + k) py + y) px + x, from
-// voxel (iz_j - pz/2 + k, iy_j - py/2 + y, ix_j - px/2 + x) of the volume,
-// laterally periodic (the grid's boundary condition); slices outside the
-// window [w0, w0 + wnz) give 0.  foci: (ix, iy, iz) triples.
-__global__ void bpm_demux_kernel(const float* __restrict__ I, int n, int w0, int wnz, const int* __restrict__ foci,
-                                 int n_foci, int px, int py, int pz, float* __restrict__ out) {
-  const long long per = (long long)px * py * pz;
-  const long long total = per * n_foci;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(i / per);
-    long long r = i - (long long)j * per;
-    const int k = (int)(r / ((long long)px * py));
-    r -= (long long)k * px * py;
-    const int y = (int)(r / px), x = (int)(r - (long long)y * px);
-    const int z = foci[3 * j + 2] - pz / 2 + k - w0;
-    float v = 0.f;
-    if (z >= 0 && z < wnz) {
-      const int yy = ((foci[3 * j + 1] - py / 2 + y) % n + n) % n;
-      const int xx = ((foci[3 * j] - px / 2 + x) % n + n) % n;
-      v = __ldcs(I + ((size_t)z * n + yy) * n + xx);
-    }
-    __stcs(out + i, v);
   }
 }
 

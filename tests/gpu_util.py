@@ -31,3 +31,17 @@ def bandlimited_field(n, dx, frac, seed, lam=0.5, n0=1.33):
     e = np.fft.ifft2(spec)
     e /= np.sqrt(np.mean(np.abs(e) ** 2))
     return e.astype(np.complex64)
+
+
+def bandlimited_field_rect(nx, ny, dx, frac, seed, lam=0.5, n0=1.33, dy=None):
+    """As bandlimited_field on an ny x nx grid (rows of nx points)."""
+    dy = dx if dy is None else dy
+    rng = np.random.default_rng(seed)
+    kx = 2 * np.pi * np.fft.fftfreq(nx, dx)
+    ky = 2 * np.pi * np.fft.fftfreq(ny, dy)
+    kp = np.sqrt(kx[None, :] ** 2 + ky[:, None] ** 2)
+    K = 2 * np.pi / lam * n0
+    spec = (rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))) * (kp < frac * K)
+    e = np.fft.ifft2(spec)
+    e /= np.sqrt(np.mean(np.abs(e) ** 2))
+    return e.astype(np.complex64)

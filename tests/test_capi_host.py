@@ -32,6 +32,12 @@ def test_bad_arguments_rejected_without_device_work(B):
     d = (B.bpm_instance_desc * 1)(B.Instance(100, 4, 0.1, 0.1).desc())
     assert lib.bpm_plan(ctypes.byref(h), d, 1, 0, None) == B.BPM_ERR_UNSUPPORTED
     assert "not one of" in B.bpm_last_error()
+    d = (B.bpm_instance_desc * 1)(B.Instance(1024, 4, 0.1, 0.1, ny=100).desc())
+    assert lib.bpm_plan(ctypes.byref(h), d, 1, 0, None) == B.BPM_ERR_UNSUPPORTED
+    # batched plans take square grids only
+    d = (B.bpm_instance_desc * 2)(B.Instance(128, 4, 0.1, 0.1).desc(), B.Instance(128, 4, 0.1, 0.1, ny=256).desc())
+    assert lib.bpm_plan(ctypes.byref(h), d, 2, 0, None) == B.BPM_ERR_UNSUPPORTED
+    assert "square" in B.bpm_last_error()
     d = (B.bpm_instance_desc * 1)(B.Instance(64, 4, 0.0, 0.1).desc())
     assert lib.bpm_plan(ctypes.byref(h), d, 1, 0, None) == B.BPM_ERR_ARG
     d = (B.bpm_instance_desc * 1)(B.Instance(64, -1, 0.1, 0.1).desc())
