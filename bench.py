@@ -65,8 +65,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT slice-loop comparison")
-    ap.add_argument("--psf-fields", type=int, default=977,
-                    help="psf1e6: multiplexed fields of 1024 foci (977 give 1.0e6 PSFs)")
+    ap.add_argument("--psf-fields", type=int, default=489,
+                    help="psf1e6: multiplexed fields of 2048 foci (489 give 1.0e6 PSFs)")
     return ap.parse_args()
 
 
@@ -537,10 +537,11 @@ def run_batch(args):
 
 
 def run_psf(args):
-    """The paper's 10^6-PSF calculation: multiplexed fields of 32 x 32 foci
-    (NA 0.6) swept over focal depths through the 1024^3 phantom; per field the
-    synthesis, the propagation down to the end of the 64-slice window around
-    the focal depth with |E|^2 written only in that window, and the
+    """The paper's 10^6-PSF calculation on its grid (light-sheet paragraph:
+    1024 x 2048 x 1024 voxels): multiplexed fields of 32 x 64 foci (pitch 32
+    px, NA 0.6) swept over focal depths through the sphere phantom; per field
+    the synthesis, the propagation down to the end of the 64-slice window
+    around the focal depth with |E|^2 written only in that window, and the
     de-multiplexing into one 32 x 32 x 64 patch per focus."""
     import torch
     from paper_1706_02261_b300 import build as build_mod
@@ -555,12 +556,12 @@ def run_psf(args):
         import torch.distributed as dist
         dist.init_process_group(backend="nccl", device_id=dev)
     stream = torch.cuda.current_stream(dev)
-    w = inputs.multiplex_1024(nz=1024)
+    w = inputs.psf_grid_1024x2048(nz=1024)
     dn = torch.from_numpy(w.dn()).to(dev)
     F = args.psf_fields
     # focal slices spread evenly over [32, 992) so that every window lies inside the volume
     depths = [32 + (k * 960) // max(F, 1) for k in range(F)]
-    s = psf.Sweep(n=w.n, nz=w.nz, d=w.d, pitch=32, depths=depths, patch=(32, 32, 64), NA=0.6, seed=2)
+    s = psf.Sweep(n=w.n, nz=w.nz, d=w.d, pitch=32, depths=depths, patch=(32, 32, 64), NA=0.6, seed=2, ny=w.rows)
     r = psf.Runner(s, dn, stream)
     # the fields are independent: each rank takes a contiguous share of the
     # depths (no collective on the data path; the slowest rank sets the time)
@@ -588,16 +589,17 @@ def run_psf(args):
     t, wall = max_over_ranks([ev0.elapsed_time(ev1) / 1e3, wall], dev, ws)
     n_psf = F * s.foci_per_field
     slices = sum(s.window(z)[1] for z in depths)
-    line = {"metric": "PSFs/s (multiplexed PSF sweep through 1024^3, 32x32x64-voxel patches)",
+    line = {"metric": "PSFs/s (multiplexed PSF sweep through 1024x2048x1024, 32x32x64-voxel patches)",
             "value": n_psf / t, "unit": "PSFs/s", "n_gpus": ws, "steps": F, "warmup": args.warmup,
             "ms_per_step": t / F * 1e3, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"psf1e6: {F} fields x {s.foci_per_field} foci (pitch 32 px, NA 0.6) through the "
-                                   "1024^3 800-sphere phantom (seed 2), focal slices 32..991, window 64 slices",
-                       "psfs": n_psf, "slices_propagated": slices, "voxel_steps": float(slices) * w.n * w.n,
+                                   f"{w.n}x{w.rows}x{w.nz} 1600-sphere phantom (seed 2), focal slices 32..991, "
+                                   "window 64 slices",
+                       "psfs": n_psf, "slices_propagated": slices, "voxel_steps": float(slices) * w.n * w.rows,
                        "seconds_for_1e6_psfs": t * 1e6 / n_psf, "wall_s": wall,
                        "paper": "10^6 PSFs 'in well under 10 minutes' on one graphics card (context)"},
-            "voxel_steps_per_s": float(slices) * w.n * w.n / t,
+            "voxel_steps_per_s": float(slices) * w.n * w.rows / t,
             "clocks": clocks.summary(), "gpu_launches": F * 7, "e2e": None, "cpu_baseline": None}
     if rank == 0:
         print(json.dumps(line), flush=True)

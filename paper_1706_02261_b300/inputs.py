@@ -223,15 +223,20 @@ class Workload:
     foci_NA: float = 0.6
     tilt_bins: tuple = (0, 0)
     extra: dict = field(default_factory=dict)
+    ny: int | None = None          # rows (the y extent); n (the x extent) when None
+
+    @property
+    def rows(self) -> int:
+        return self.ny or self.n
 
     @property
     def voxels(self) -> int:
-        return self.n * self.n * self.nz
+        return self.n * self.rows * self.nz
 
     def dn(self, threads: int | None = None) -> np.ndarray:
         if self.seed is None:
             return single_sphere_dn(self.n, self.nz, self.d)
-        return sphere_phantom_dn((self.nz, self.n, self.n), self.d, self.n_spheres, self.seed,
+        return sphere_phantom_dn((self.nz, self.rows, self.n), self.d, self.n_spheres, self.seed,
                                  threads=threads)
 
     def foci(self) -> FociSet:
@@ -258,6 +263,15 @@ def multiplex_1024(nz: int = 1024) -> Workload:
     lattice, NA 0.6, random phases, one seeded focal depth."""
     return Workload("multiplex1024", 1024, nz, 0.1625, input_kind="foci", seed=2,
                     n_spheres=800, foci_per_side=32, foci_NA=0.6)
+
+
+def psf_grid_1024x2048(nz: int = 1024) -> Workload:
+    """The lateral grid of the paper's 10^6-PSF calculation (light-sheet
+    paragraph: 1024 x 2048 x 1024 voxels): nx = 1024, ny = 2048, dx = dz =
+    0.1625 um, the sphere phantom recipe of the 1024^3 workload at the same
+    density (1600 spheres, seed 2)."""
+    return Workload("psf1024x2048", 1024, nz, 0.1625, input_kind="foci", seed=2,
+                    n_spheres=1600, foci_NA=0.6, ny=2048)
 
 
 BATCH_SIZES = (128, 192, 256, 384, 512)

@@ -30,7 +30,7 @@ from . import bpm as B
 
 @dataclass
 class Sweep:
-    n: int                      # lateral grid (n x n)
+    n: int                      # lateral grid: n points along x (ny rows along y)
     nz: int                     # slices of the volume
     d: float                    # dx = dy = dz, um
     pitch: int                  # lattice pitch of the foci, pixels
@@ -41,12 +41,18 @@ class Sweep:
     n0: float = 1.33
     seed: int = 0
     offset: int = field(default=-1)   # lattice offset in pixels (default pitch // 2)
+    ny: int | None = None       # rows along y (n when None)
+
+    @property
+    def rows(self) -> int:
+        return self.ny or self.n
 
     def lattice(self):
-        """(ix, iy) of the foci of one field: a pitch-spaced square lattice."""
+        """(ix, iy) of the foci of one field: a pitch-spaced lattice over the grid."""
         off = self.pitch // 2 if self.offset < 0 else self.offset
         ax = np.arange(off, self.n, self.pitch)
-        iy, ix = np.meshgrid(ax, ax, indexing="ij")
+        ay = np.arange(off, self.rows, self.pitch)
+        iy, ix = np.meshgrid(ay, ax, indexing="ij")
         return ix.ravel().astype(np.int64), iy.ravel().astype(np.int64)
 
     @property
@@ -81,10 +87,10 @@ class Runner:
         self.dn = dn
         self.stream = stream
         dev = dn.device
-        self.plan = B.bpm_plan(B.Instance(s.n, s.nz, s.d, s.d, s.lam, s.n0))
-        self.e0 = torch.empty((s.n, s.n), dtype=torch.complex64, device=dev)
+        self.plan = B.bpm_plan(B.Instance(s.n, s.nz, s.d, s.d, s.lam, s.n0, ny=s.rows))
+        self.e0 = torch.empty((s.rows, s.n), dtype=torch.complex64, device=dev)
         self.e1 = torch.empty_like(self.e0)
-        self.win = torch.empty((s.patch[2], s.n, s.n), dtype=torch.float32, device=dev)
+        self.win = torch.empty((s.patch[2], s.rows, s.n), dtype=torch.float32, device=dev)
 
     def field(self, k: int, out) -> None:
         """PSF patches of field k into out [foci_per_field][pz][py][px]."""
