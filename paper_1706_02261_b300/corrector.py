@@ -276,8 +276,13 @@ def evaluate_volume(cs: CropSetup, seed: int, corr: "B.Corrector | None", dev, d
                "coarse_field": float(torch.linalg.vector_norm(ec - ef) / nrm),
                "coarse_intensity": float((Ic - ref_planes).abs().max() / peak)}
         if corr is not None:
+            # one corrected step outside the timed region (first-use set-up of
+            # the kernels it launches)
             e = E0.clone()
             Icor = torch.empty_like(Ic)
+            B.bpm_propagate(coarse, dnc, e, e, None, 0, 1)
+            corr.apply(e, dnc[0] if s.c_in == 3 else None, s.dn_scale)
+            torch.mul(e.real, e.real, out=Icor[0]).addcmul_(e.imag, e.imag)
             ev[4].record()
             for j in range(nzc):
                 B.bpm_propagate(coarse, dnc, e, e, None, j, j + 1)

@@ -1311,7 +1311,7 @@ __global__ void bpm_static_twiddle_kernel(float2* out, TwSchedule s) {
   const double ang = s.sign * 6.283185307179586 * (double)ex / (double)(Ns * R);
   double sn, cs;
   sincos(ang, &sn, &cs);
-  out[(size_t)(p - 1) * s.n + twiddle_slot(b, r, t, R, s.t, s.paired != 0)] = make_float2((float)cs, (float)sn);
+  out[(size_t)(p - 1) * s.n + twiddle_slot(b, r, t, R, s.t, s.paired != 0)] = round_unit(cs, sn);
 }
 
 int launch_static_twiddles(const TwSchedule& s, float2* dst, cudaStream_t stream) {

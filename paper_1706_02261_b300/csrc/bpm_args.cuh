@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace bpmk {
 
 constexpr int kThreads = 256;   // CTA size for every kernel of the path
@@ -101,6 +103,43 @@ struct BatchArgs {
 // table builders both use it, so their layouts cannot drift apart.
 __host__ __device__ inline size_t twiddle_slot(int b, int r, int t, int R, int T, bool paired) {
   return paired ? ((size_t)(b * (R / 2) + r / 2) * T + t) * 2 + (r & 1) : (size_t)(b * R + r) * T + t;
+}
+
+// Rounding of a unit-modulus twiddle (c, s) = (cos, sin) to FP32.  The
+// transforms apply the same twiddles in every slice, so their rounding errors
+// add up coherently over the depth, and the modulus error |w|^2 - 1 is the
+// part that does not cancel between a transform and its inverse.  Of the 3 x 3
+// pairs one ulp around the round-to-nearest pair, this takes the one whose
+// squared modulus (in FP64) is closest to 1, ties to the nearer pair: the
+// modulus error falls from 3.3e-8 to 2.2e-8 rms over the 1024-point
+// twiddles, and the field error of 1024 homogeneous 1024^2 slices from
+// 1.58e-4 to 1.14e-4 (a wider search trades too much angle for modulus and
+// was worse: 1.98e-4 at two ulps).
+__host__ __device__ inline float ulp_step(float x, int dir) {
+  if (dir == 0) return x;
+#ifdef __CUDA_ARCH__
+  return nextafterf(x, dir > 0 ? 1e30f : -1e30f);
+#else
+  return std::nextafter(x, dir > 0 ? 1e30f : -1e30f);
+#endif
+}
+__host__ __device__ inline float2 round_unit(double c, double s) {
+  const float c0 = (float)c, s0 = (float)s;
+  float2 best = make_float2(c0, s0);
+  double bm = 1e300, bd = 1e300;
+  for (int i = -1; i <= 1; ++i)
+    for (int j = -1; j <= 1; ++j) {
+      const float cc = ulp_step(c0, i), ss = ulp_step(s0, j);
+      const double m = (double)cc * cc + (double)ss * ss - 1.0;
+      const double am = m < 0 ? -m : m;
+      const double d = ((double)cc - c) * ((double)cc - c) + ((double)ss - s) * ((double)ss - s);
+      if (am < bm || (am == bm && d < bd)) {
+        bm = am;
+        bd = d;
+        best = make_float2(cc, ss);
+      }
+    }
+  return best;
 }
 
 }  // namespace bpmk

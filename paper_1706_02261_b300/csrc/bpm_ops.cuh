@@ -13,7 +13,7 @@ namespace bpmk {
 
 constexpr double kTwoPiHost = 6.283185307179586;
 
-// Host-built twiddle table of one transform (FP64, rounded once): for every
+// Host-built twiddle table of one transform (FP64, rounded by round_unit): for every
 // pass p >= 1 of the radix list, N entries holding W_{Ns R}^{(j mod Ns) r},
 // j = t + b T, with the transform's sign, at twiddle_slot(b, r, t).
 inline void append_twiddles(std::vector<float2>& out, int N, int T, const std::vector<int>& radices, int sign,
@@ -31,7 +31,7 @@ inline void append_twiddles(std::vector<float2>& out, int N, int T, const std::v
             const int j = t + b * T;
             const long long e = (long long)(j % Ns) * r % (long long)(Ns * R);
             const double ang = sign * kTwoPiHost * (double)e / (double)(Ns * R);
-            out[base + twiddle_slot(b, r, t, R, T, paired)] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            out[base + twiddle_slot(b, r, t, R, T, paired)] = round_unit(std::cos(ang), std::sin(ang));
           }
     }
     Ns *= R;
@@ -63,7 +63,7 @@ void cfg_twiddles_host(std::vector<float2>& v) {
         for (int k = 2 * kp; k < 2 * kp + 2; ++k) {
           const long long e = (long long)a * k % N;
           const double ang = -kTwoPiHost * (double)e / (double)N;
-          v.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+          v.push_back(round_unit(std::cos(ang), std::sin(ang)));
         }
   }
 }

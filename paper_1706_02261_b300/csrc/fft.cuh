@@ -24,9 +24,9 @@
 //
 // Twiddles between passes come from a per-thread table in shared memory
 // (laid out [pass][b][r][t], so reads are bank-conflict free), built in FP64
-// on the host and rounded once to float.  Constant twiddles inside the
-// register DFTs are compile-time values of cos/sin evaluated by a constexpr
-// Taylor series.
+// on the host and rounded once to float (round_unit).  Constant twiddles
+// inside the register DFTs are compile-time values of cos/sin evaluated by a
+// constexpr Taylor series and rounded the same way (ct_unit).
 #pragma once
 #include <cuda_runtime.h>
 #include <utility>
@@ -60,6 +60,39 @@ __host__ __device__ constexpr double ct_angle(int e, int R) {
   int m = ((e % R) + R) % R;
   double a = 2.0 * kPiD * (double)m / (double)R;
   return a > kPiD ? a - 2.0 * kPiD : a;
+}
+
+// Compile-time counterpart of round_unit (bpm_args.cuh) for the constant
+// twiddles inside the register DFTs: one ulp of a normal float, and the pair
+// one ulp around the rounded (c, s) whose squared modulus is closest to 1.
+__host__ __device__ constexpr double ct_ulp(float x) {
+  double a = x < 0 ? -(double)x : (double)x;
+  if (a == 0.0) return 1.401298464324817e-45;
+  double p = 1.0;
+  while (p > a) p *= 0.5;
+  while (p * 2.0 <= a) p *= 2.0;
+  return p / 8388608.0;   // 2^-23 of the binade of x
+}
+struct CtPair {
+  float c, s;
+};
+__host__ __device__ constexpr CtPair ct_unit(double c, double s) {
+  const float c0 = (float)c, s0 = (float)s;
+  CtPair best{c0, s0};
+  double bm = 1e300, bd = 1e300;
+  for (int i = -1; i <= 1; ++i)
+    for (int j = -1; j <= 1; ++j) {
+      const float cc = (float)((double)c0 + i * ct_ulp(c0)), ss = (float)((double)s0 + j * ct_ulp(s0));
+      const double m = (double)cc * cc + (double)ss * ss - 1.0;
+      const double am = m < 0 ? -m : m;
+      const double d = ((double)cc - c) * ((double)cc - c) + ((double)ss - s) * ((double)ss - s);
+      if (am < bm || (am == bm && d < bd)) {
+        bm = am;
+        bd = d;
+        best = CtPair{cc, ss};
+      }
+    }
+  return best;
 }
 
 template <int... Is, class F>
@@ -112,9 +145,8 @@ __device__ __forceinline__ float2 twc(float2 a) {
   } else if constexpr (4 * e == 3 * R) {
     return mul_si<-S>(a);
   } else {
-    constexpr float c = (float)ct_cos(ct_angle(e, R));
-    constexpr float s = (float)(S * ct_sin(ct_angle(e, R)));
-    return cmul(a, make_float2(c, s));
+    constexpr CtPair w = ct_unit(ct_cos(ct_angle(e, R)), S * ct_sin(ct_angle(e, R)));
+    return cmul(a, make_float2(w.c, w.s));
   }
 }
 

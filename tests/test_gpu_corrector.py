@@ -120,6 +120,34 @@ def test_training_gains_over_coarse_steps_on_held_out_seeds(B, c_in, min_gain):
         corr.free()
 
 
+@pytest.mark.parametrize("c_in,min_gain", [(2, 1.05), (3, 1.5)])
+def test_crop_pairs_gain_on_held_out_volumes(B, c_in, min_gain):
+    """The workload's recipe at 256^3: pairs as 128^2 crops of full fine-step
+    fields (seeds 4000-4011, 256 crops each), held-out volumes 5000-5003
+    through coarse steps with and without the corrector, errors against
+    fine-step BPM: the field error falls by min_gain, and (3 channels) the
+    intensity error falls as well."""
+    from paper_1706_02261_b300 import corrector as C
+    dev = torch.device("cuda")
+    cs = C.CropSetup(n=256, nz=256, crop=128, c_in=c_in)
+    corr = B.Corrector(c_in, 32, cs.n, cs.n)
+    try:
+        corr.set_params(inputs.corrector_init(c_in, 0).astype(np.float32))
+        X, T = C.make_crop_pairs(cs, range(4000, 4012), corr, dev, 256, rng_seed=c_in)
+        corr.set_residual_scale(C.residual_scale(corr, X, T, batch=32))
+        C.train(corr, X, T, steps=3000, batch=32, lr=1e-3, seed=1)
+        del X, T
+        rows = [C.evaluate_volume(cs, sd, corr, dev) for sd in range(5000, 5004)]
+        gain = np.mean([r["coarse_field"] for r in rows]) / np.mean([r["corrected_field"] for r in rows])
+        igain = np.mean([r["coarse_intensity"] for r in rows]) / np.mean([r["corrected_intensity"] for r in rows])
+        print(f"c_in={c_in} field gain {gain:.2f} intensity gain {igain:.2f} rows={rows}")
+        assert gain > min_gain, rows
+        if c_in == 3:
+            assert igain > 1.2, rows
+    finally:
+        corr.free()
+
+
 @pytest.mark.parametrize("c_in,h,w", [(2, 32, 128), (3, 16, 256)])
 def test_tensor_core_forward_matches_bf16_activation_oracle(B, c_in, h, w):
     """The tcgen05 inference engine (BF16 activations and weights, FP32
