@@ -479,7 +479,7 @@ def run_batch(args):
     eout = [torch.empty_like(e) for e in eins]
     inten = [torch.empty((w.nz, w.n, w.n), dtype=torch.float32, device=dev) for w in ws]
     t0 = time.perf_counter()
-    B.bpm_autotune(plan, dns, eins, eout, inten, 4, stream)
+    B.bpm_autotune(plan, dns, eins, eout, inten, 32, stream)
     tune_s = time.perf_counter() - t0
     info = B.bpm_plan_info(plan)
     for _ in range(args.warmup):
@@ -524,7 +524,8 @@ def run_batch(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch64: 64 seeded instances (default_rng(3)), sizes {128,192,256,384,512}^2, "
                                    "128-512 slices, tilted plane waves or 8x8 foci NA 0.6, phantoms seeds 3000+k",
-                       "voxel_steps": vox, "cluster_ctas": info["team_ctas"], "autotune_s": tune_s,
+                       "voxel_steps": vox, "cluster_ctas": info["team_ctas"], "schedule_set": info["schedule"],
+                       "autotune_s": tune_s,
                        "graph": True},
             "sequential_single_plans": {"ms_per_step": t_seq * 1e3, "value": vox / t_seq,
                                         "speedup_batched": t_seq / t_batch},

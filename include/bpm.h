@@ -295,28 +295,32 @@ const char *bpm_last_error(void);
  * out[0] = team CTAs, out[1] = threads per CTA, out[2] = dynamic shared
  * memory bytes, out[3] = persistent (1) or multi-launch (0), out[4] = kernel
  * launches per bpm_propagate call, out[5] = transform schedule in use,
- * out[6] = number of schedules of the plan's grid size (single-field plans;
- * batched plans report 0 and 1).  n_out may be smaller than 7. */
+ * out[6] = number of schedules of the plan's grid size (batched plans: the
+ * schedule set of the batched kernel and the number of sets).  n_out may be
+ * smaller than 7. */
 int bpm_plan_info(bpm_plan_t p, int *out, int n_out);
 
 /* bpm_autotune - time the propagation of slices [0, z_probe) on the given
- * buffers and keep the fastest configuration for later calls.  Batched plans:
- * every instance with each cluster size (2, 4, 8, 16 CTAs per team).
+ * buffers and keep the fastest configuration for later calls (this is where
+ * the team sizes and radix schedules of batched propagation are picked).  Batched
+ * plans: every instance, with each transform schedule set of the batched
+ * kernel (three sets of radix order and pass structure for the 256, 512 and
+ * 1024 transforms) and each cluster size (2, 4, 8, 16 CTAs per team).
  * Single-field plans: each transform schedule of the grid size (radix order
  * and pass structure of the row and column transforms: square grids of 256
- * and 512 have three, 1024 two, the other grids one).  Overwrites d_Eout and the first z_probe
- * intensity slices; synchronises the stream (and the device when the
- * schedule changes).  Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
+ * and 512 have three, 1024 two, the other grids one).  Overwrites d_Eout and
+ * the first z_probe intensity slices; synchronises the stream (and the device
+ * when the schedule changes).  Errors: BPM_ERR_ARG, BPM_ERR_CUDA. */
 int bpm_autotune(bpm_plan_t p, const void *const *d_dn, const void *const *d_Ein, void *const *d_Eout,
                  float *const *d_I, int z_probe, cudaStream_t stream);
 
-/* bpm_set_schedule - single-field plans: use transform schedule `schedule`
- * (0 .. out[6] - 1 of bpm_plan_info; a square plan starts with the schedule
+/* bpm_set_schedule - use transform schedule `schedule` (0 .. out[6] - 1 of
+ * bpm_plan_info).  Single-field plans: a square plan starts with the schedule
  * measured fastest for its size, 2 for 512 and 0 for the others; the rows and
- * columns of a rectangular grid each take their length's).
- * Results of every schedule agree to FP32 rounding.  Synchronises the device
- * when the schedule changes.  Errors: BPM_ERR_ARG (NULL plan, schedule out of
- * range), BPM_ERR_UNSUPPORTED (batched plan), BPM_ERR_CUDA. */
+ * columns of a rectangular grid each take their length's.  Batched plans: the
+ * schedule set of the batched kernel (starts at 0).  Results of every
+ * schedule agree to FP32 rounding.  Synchronises the device when the schedule
+ * changes.  Errors: BPM_ERR_ARG (NULL plan, schedule out of range), BPM_ERR_CUDA. */
 int bpm_set_schedule(bpm_plan_t p, int schedule);
 
 /* bpm_debug_set_barrier_timeout - test hook: device barrier wait limit in

@@ -11,10 +11,11 @@ ROOT = os.path.dirname(HERE)
 # group of transform lengths (ops_*.cu), the batched kernel, the corrector;
 # the slowest first, so that the parallel compilation ends sooner
 SRCS = [os.path.join(HERE, "csrc", f) for f in
-        ("ops_1024.cu", "ops_2048.cu", "batch.cu", "ops_512.cu", "ops_256.cu", "ops_384.cu", "ops_small.cu",
-         "bpm.cu", "corrector.cu")]
+        ("ops_1024.cu", "ops_2048.cu", "batch0.cu", "batch1.cu", "batch2.cu", "ops_512.cu", "ops_256.cu",
+         "ops_384.cu", "ops_small.cu", "bpm.cu", "corrector.cu")]
 DEPS = SRCS + [os.path.join(HERE, "csrc", f) for f in
-               ("bpm_kernels.cuh", "bpm_args.cuh", "bpm_aux_kernels.cuh", "bpm_ops.cuh", "bpm_ops.h", "fft.cuh")] + \
+               ("bpm_kernels.cuh", "bpm_args.cuh", "bpm_aux_kernels.cuh", "bpm_ops.cuh", "bpm_ops.h", "batch.cuh",
+                "fft.cuh")] + \
        [os.path.join(ROOT, "include", f) for f in ("bpm.h", "bpm_corrector.h")]
 LIB = os.path.join(HERE, "libbpm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

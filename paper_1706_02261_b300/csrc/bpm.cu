@@ -172,6 +172,8 @@ struct bpm_plan_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   size_t batch_smem = 0;
   int cluster = 8;                  // CTAs per team (cluster size), set by bpm_autotune
+  int batch_set = 0;                // transform schedule set of the batched kernel, set by bpm_autotune
+  BatchKernel bk;                   // the batched kernel of that set
   bool have_args = false;           // h_inst holds the arguments of the last call
   cudaStream_t cap = nullptr;       // capture stream for BPM_FLAG_GRAPH
   cudaGraphExec_t gexec = nullptr;
@@ -187,14 +189,23 @@ struct bpm_plan_s {
 
 namespace {
 
-// schedules of the row and column lengths of instance i
+// schedules of the row and column lengths of instance i (batched plans: the
+// schedule set of the batched kernel)
 int row_sched_of(const bpm_plan_s* p, const bpm_instance_desc& d) {
-  if (p->inst.size() > 1) return 0;
+  if (p->inst.size() > 1) return p->bk.sched_of(d.nx);
   return d.nx == d.ny ? p->sched : default_schedule(d.nx);
 }
 int col_sched_of(const bpm_plan_s* p, const bpm_instance_desc& d) {
-  if (p->inst.size() > 1) return 0;
+  if (p->inst.size() > 1) return p->bk.sched_of(d.ny);
   return d.nx == d.ny ? p->sched : default_schedule(d.ny);
+}
+
+BatchKernel batch_kernel(int set) {
+  switch (set) {
+    case 1: return batch_kernel_1();
+    case 2: return batch_kernel_2();
+    default: return batch_kernel_0();
+  }
 }
 
 // The plan's resources for length n in schedule s: kernels' shared-memory
@@ -500,17 +511,33 @@ int max_active_clusters(bpm_plan_s* p, int cl, int* out) {
   cfg.dynamicSmemBytes = p->batch_smem;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  BPM_CU(cudaOccupancyMaxActiveClusters(out, batch_kernel_fn(), &cfg));
+  BPM_CU(cudaOccupancyMaxActiveClusters(out, p->bk.fn, &cfg));
+  return BPM_OK;
+}
+
+// The batched kernel of schedule set `set`: the tables of its schedules for
+// the plan's sizes, its shared memory (the largest need of those sizes) and
+// launch attributes.
+int use_batch_set(bpm_plan_s* p, int set) {
+  p->batch_set = set;
+  p->bk = batch_kernel(set);
+  size_t smem = 0;
+  for (const InstPlan& in : p->inst) {
+    LenRes* lr = nullptr;
+    int rc = use_length(p, in.d.nx, p->bk.sched_of(in.d.nx), &lr);
+    if (rc) return rc;
+    smem = std::max(smem, lr->ops->smem);
+  }
+  p->batch_smem = smem;
+  BPM_CU(cudaFuncSetAttribute(p->bk.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BPM_CU(cudaFuncSetAttribute(p->bk.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   return BPM_OK;
 }
 
 int setup_batch(bpm_plan_s* p) {
   const int n = (int)p->inst.size();
-  size_t smem = 0;
-  for (auto& kv : p->lens) smem = std::max(smem, kv.second.ops->smem);
-  p->batch_smem = smem;
-  BPM_CU(cudaFuncSetAttribute(batch_kernel_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  BPM_CU(cudaFuncSetAttribute(batch_kernel_fn(), cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  int rc0 = use_batch_set(p, 0);
+  if (rc0) return rc0;
   BPM_CU(cudaMalloc(&p->d_inst, sizeof(InstArgs) * n));
   BPM_CU(cudaMalloc(&p->d_order, sizeof(int) * n));
   BPM_CU(cudaMalloc(&p->d_queue, sizeof(unsigned long long)));
@@ -588,7 +615,7 @@ int enqueue_batch(bpm_plan_s* p, int clusters, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void* kargs[] = {&b};
-  BPM_CU(cudaLaunchKernelExC(&cfg, batch_kernel_fn(), kargs));
+  BPM_CU(cudaLaunchKernelExC(&cfg, p->bk.fn, kargs));
   if (use_fill) {
     BPM_CU(cudaStreamWaitEvent(p->fill_stream, p->ev_fork, 0));
     BatchArgs f = b;
@@ -599,7 +626,7 @@ int enqueue_batch(bpm_plan_s* p, int clusters, cudaStream_t s) {
     cfg.gridDim = dim3(fill * kFillCluster);
     cfg.stream = p->fill_stream;
     void* fargs[] = {&f};
-    BPM_CU(cudaLaunchKernelExC(&cfg, batch_kernel_fn(), fargs));
+    BPM_CU(cudaLaunchKernelExC(&cfg, p->bk.fn, fargs));
     BPM_CU(cudaEventRecord(p->ev_join, p->fill_stream));
     BPM_CU(cudaStreamWaitEvent(s, p->ev_join, 0));
   }
@@ -614,7 +641,7 @@ int propagate_batch(bpm_plan_s* p, const void* const* d_dn, const void* const* d
   std::memset(args.data(), 0, sizeof(InstArgs) * n);
   for (int i = 0; i < n; ++i) {
     const InstPlan& in = p->inst[i];
-    const LenRes& r = p->lens[std::make_pair(in.d.nx, 0)];
+    const LenRes& r = p->lens[std::make_pair(in.d.nx, p->bk.sched_of(in.d.nx))];
     InstArgs& a = args[i];
     a.work = static_cast<float2*>(d_Eout[i]);
     a.ein = static_cast<const float2*>(d_Ein[i]);
@@ -741,11 +768,7 @@ extern "C" int bpm_plan(bpm_plan_t* out, const bpm_instance_desc* inst, int n_in
       p->sched = d.nx == d.ny ? default_schedule(d.nx) : 0;
       rc = setup_single(p);
     } else {
-      for (int i = 0; i < n_inst && rc == BPM_OK; ++i) {
-        LenRes* lr = nullptr;
-        rc = use_length(p, inst[i].nx, 0, &lr);
-      }
-      if (rc == BPM_OK) rc = setup_batch(p);
+      rc = setup_batch(p);
     }
   }
   if (rc == BPM_OK) cu(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
@@ -1074,8 +1097,8 @@ extern "C" int bpm_plan_info(bpm_plan_t p, int* out, int n_out) {
     vals[2] = (int)p->batch_smem;
     vals[3] = 1;
     vals[4] = 1;
-    vals[5] = 0;
-    vals[6] = 1;
+    vals[5] = p->batch_set;
+    vals[6] = kBatchKernels;
   }
   for (int i = 0; i < n_out && i < 7; ++i) out[i] = vals[i];
   return BPM_OK;
@@ -1199,7 +1222,18 @@ int autotune_schedule(bpm_plan_s* p, const void* const* d_dn, const void* const*
 
 extern "C" int bpm_set_schedule(bpm_plan_t p, int schedule) {
   if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
-  if (p->inst.size() != 1) return fail(BPM_ERR_UNSUPPORTED, "schedules are chosen for single-field plans only");
+  if (p->inst.size() != 1) {
+    if (schedule < 0 || schedule >= kBatchKernels)
+      return fail(BPM_ERR_ARG, "batched plans have schedule sets 0..%d, not %d", kBatchKernels - 1, schedule);
+    if (schedule == p->batch_set) return BPM_OK;
+    BPM_CU(cudaDeviceSynchronize());
+    p->have_args = false;
+    if (p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    return use_batch_set(p, schedule);
+  }
   const bpm_instance_desc& d = p->inst[0].d;
   const int count = d.nx == d.ny ? schedule_count(d.nx) : 1;
   if (schedule < 0 || schedule >= count)
@@ -1212,42 +1246,50 @@ extern "C" int bpm_autotune(bpm_plan_t p, const void* const* d_dn, const void* c
   if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
   if (z_probe < 1) return fail(BPM_ERR_ARG, "z_probe must be >= 1");
   if (p->inst.size() < 2) return autotune_schedule(p, d_dn, d_Ein, d_Eout, d_I, z_probe, stream);
-  const int keep = p->cluster;
+  // batched plans: every schedule set of the batched kernel with every
+  // cluster size, one warm-up and one timed call each
+  const int keep_cl = p->cluster, keep_set = p->batch_set;
   const unsigned keep_flags = p->flags;
   p->flags &= ~(unsigned)BPM_FLAG_GRAPH;
   float best = 1e30f;
-  int best_cl = keep;
+  int best_cl = keep_cl, best_set = keep_set;
   cudaEvent_t e0, e1;
   BPM_CU(cudaEventCreate(&e0));
   BPM_CU(cudaEventCreate(&e1));
-  for (int cl : {2, 4, 8, 16}) {
-    int clusters = 0;
-    p->cluster = cl;
-    if (max_active_clusters(p, cl, &clusters) != BPM_OK || clusters < 1) continue;
-    int rc = bpm_propagate(p, d_dn, d_Ein, d_Eout, d_I, 0, z_probe, stream);   // warm-up
-    if (rc == BPM_OK) {
-      cudaEventRecord(e0, stream);
-      rc = bpm_propagate(p, d_dn, d_Ein, d_Eout, d_I, 0, z_probe, stream);
-      cudaEventRecord(e1, stream);
-    }
-    if (rc != BPM_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) {
-      best = ms;
-      best_cl = cl;
+  for (int set = 0; set < kBatchKernels; ++set) {
+    if (use_batch_set(p, set) != BPM_OK) continue;
+    for (int cl : {2, 4, 8, 16}) {
+      int clusters = 0;
+      p->cluster = cl;
+      if (max_active_clusters(p, cl, &clusters) != BPM_OK || clusters < 1) continue;
+      int rc = bpm_propagate(p, d_dn, d_Ein, d_Eout, d_I, 0, z_probe, stream);   // warm-up
+      if (rc == BPM_OK) {
+        cudaEventRecord(e0, stream);
+        rc = bpm_propagate(p, d_dn, d_Ein, d_Eout, d_I, 0, z_probe, stream);
+        cudaEventRecord(e1, stream);
+      }
+      if (rc != BPM_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_cl = cl;
+        best_set = set;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaGetLastError();
-  p->cluster = best_cl;
   p->flags = keep_flags;
   p->have_args = false;
   if (p->gexec) {
     cudaGraphExecDestroy(p->gexec);
     p->gexec = nullptr;
   }
+  const int rc = use_batch_set(p, best_set);
+  p->cluster = best_cl;
+  if (rc) return rc;
   return bpm_check(p);
 }
 

@@ -1171,10 +1171,10 @@ __device__ __forceinline__ unsigned cluster_id() {
   return r;
 }
 
-template <int N>
+template <class C>
 __device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int rank, int CL, float2* smem,
                                                bool& bad) {
-  using C = Cfg<N>;
+  constexpr int N = C::N;
   float2* s_twf = smem;
   float2* s_twi = s_twf + C::TWF;
   float2* s_buf = s_twi + C::TWI + C::TW4;

@@ -55,8 +55,17 @@ const LenOps* find_len_ops(int n, int sched);
 const PairOps* find_pair_ops(int nx, int ny, int sched);
 const std::vector<int>& supported_lengths();
 
-// the batched kernel (batch.cu)
-const void* batch_kernel_fn();
+// the batched kernel in one schedule set (batch0.cu .. batch2.cu): the
+// kernel and the schedules of the 256, 512 and 1024 transforms it uses
+struct BatchKernel {
+  const void* fn = nullptr;
+  int sched[3] = {0, 0, 0};
+  int sched_of(int n) const { return n == 256 ? sched[0] : (n == 512 ? sched[1] : (n == 1024 ? sched[2] : 0)); }
+};
+constexpr int kBatchKernels = 3;
+BatchKernel batch_kernel_0();
+BatchKernel batch_kernel_1();
+BatchKernel batch_kernel_2();
 
 // one call per translation unit of kernels (bpm.cu calls them all)
 struct OpsRegistry {

@@ -31,10 +31,13 @@ def _mixed_batch():
     return cases
 
 
-def _run_batch(B, cases, flags=0, tune=False, z=(0, 2 ** 31 - 1)):
+def _run_batch(B, cases, flags=0, tune=False, z=(0, 2 ** 31 - 1), sched=None):
     dev = torch.device("cuda")
     plan = B.bpm_plan([B.Instance(n, nz, d, d) for (n, nz, d, _, _) in cases], flags=flags)
     try:
+        if sched is not None:
+            B.bpm_set_schedule(plan, sched)
+            assert B.bpm_plan_info(plan)["schedule"] == sched
         dn = [torch.from_numpy(c[3]).to(dev) for c in cases]
         ein = [torch.from_numpy(c[4]).to(dev) for c in cases]
         eout = [torch.empty_like(e) for e in ein]
@@ -43,7 +46,7 @@ def _run_batch(B, cases, flags=0, tune=False, z=(0, 2 ** 31 - 1)):
             B.bpm_autotune(plan, dn, ein, eout, inten, 2)
             info = B.bpm_plan_info(plan)
             assert info["team_ctas"] in (2, 4, 8, 16)
-            assert (info["schedule"], info["schedules"]) == (0, 1)     # the batched kernel's own schedules
+            assert info["schedules"] == 3 and 0 <= info["schedule"] < 3    # schedule sets of the batched kernel
         B.bpm_propagate(plan, dn, ein, eout, inten, *z)
         assert B.bpm_check(plan) == B.BPM_OK, B.bpm_last_error()
         out1 = [e.cpu().numpy() for e in eout]
@@ -60,10 +63,12 @@ def _run_batch(B, cases, flags=0, tune=False, z=(0, 2 ** 31 - 1)):
         B.bpm_free(plan)
 
 
-@pytest.mark.parametrize("flags,tune", [(0, False), (4, False), (4, True)])
-def test_mixed_batch_matches_oracle(B, flags, tune):
+@pytest.mark.parametrize("flags,tune,sched", [(0, False, 0), (4, False, 0), (4, True, None), (4, False, 1),
+                                              (0, False, 2)])
+def test_mixed_batch_matches_oracle(B, flags, tune, sched):
+    """Every schedule set of the batched kernel (and the autotuned one)."""
     cases = _mixed_batch()
-    E, I = _run_batch(B, cases, flags=flags, tune=tune)
+    E, I = _run_batch(B, cases, flags=flags, tune=tune, sched=sched)
     for (n, nz, d, dn16, E0), Eg, Ig in zip(cases, E, I):
         if nz == 0:
             assert np.array_equal(Eg, E0)            # empty slice range copies the input
