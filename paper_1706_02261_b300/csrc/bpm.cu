@@ -131,7 +131,7 @@ struct GridRes {
   int team = 0;                   // CTAs per field
   size_t smem_persist = 0;        // dynamic shared memory with the staging buffers
   int rmax_r = 0, rmax_c = 0;     // rows / columns per team CTA at most
-  int h_res = 0, dn_stage = 0, i_stage = 0;
+  int h_res = 0, dn_stage = 0;
 };
 
 struct InstPlan {
@@ -241,9 +241,9 @@ int use_length(bpm_plan_s* p, int n, int s, LenRes** out) {
 // Team and shared-memory staging of the persistent kernel of a grid: the
 // smallest team that gives every group one row and one column per half-step
 // (every SM takes rows with the four-step column layout), at most one CTA per
-// SM; the staging buffers of propagator columns, index rows and intensity rows
-// are dropped (in that order) when they would not fit next to the tables and
-// group buffers.
+// SM; the staging buffers of propagator columns and index rows are dropped
+// (in that order) when they would not fit next to the tables and group
+// buffers.
 void grid_config(const PairOps* o, int nx, int ny, int sms, size_t max_optin, GridRes& g) {
   const int want = o->four_step ? ny : std::max((ny + o->row_ng - 1) / o->row_ng, (nx + o->col_ng - 1) / o->col_ng);
   g.ops = o;
@@ -252,15 +252,13 @@ void grid_config(const PairOps* o, int nx, int ny, int sms, size_t max_optin, Gr
   const int cper = (nx + g.team - 1) / g.team;
   g.rmax_c = (cper + o->col_ng - 1) / o->col_ng * o->col_ng;
   auto rup = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  const size_t hb = rup((size_t)g.rmax_c * o->col_hs * sizeof(float2)), db = rup((size_t)g.rmax_r * nx * 2),
-               ib = rup((size_t)g.rmax_r * nx * sizeof(float));
+  const size_t hb = rup((size_t)g.rmax_c * o->col_hs * sizeof(float2)), db = rup((size_t)g.rmax_r * nx * 2);
   const size_t budget = max_optin - 1024;   // static shared memory of the kernel
   const size_t base = o->smem_base;
-  g.h_res = g.dn_stage = g.i_stage = 1;
-  if (base + hb + db + ib > budget) g.h_res = 0;
-  if (base + db + ib > budget) g.i_stage = 0;
+  g.h_res = g.dn_stage = 1;
+  if (base + hb + db > budget) g.h_res = 0;
   if (base + db > budget) g.dn_stage = 0;
-  g.smem_persist = base + (g.h_res ? hb : 0) + (g.dn_stage ? db : 0) + (g.i_stage ? ib : 0);
+  g.smem_persist = base + (g.h_res ? hb : 0) + (g.dn_stage ? db : 0);
 }
 
 // The persistent kernel of a single-field plan's grid in its schedule, when
@@ -450,7 +448,6 @@ int launch_propagate(bpm_plan_s* p, const InstPlan& in, StepArgs a, cudaStream_t
   a.rmax_c = g.rmax_c;
   a.h_res = g.h_res;
   a.dn_stage = g.dn_stage;
-  a.i_stage = g.i_stage;
   BPM_CU(cudaMemsetAsync(p->bar, 0, sizeof(unsigned), s));
   void* args[] = {&a};
   BPM_CU(cudaLaunchCooperativeKernel(g.ops->kernel[a.kappa ? 1 : 0], dim3(g.team), dim3(kThreads), args,
@@ -1434,7 +1431,6 @@ int static_propagate(const bpm_instance_desc& d, unsigned char* scratch, const v
   a.rmax_c = r.rmax_c;
   a.h_res = r.h_res;
   a.dn_stage = r.dn_stage;
-  a.i_stage = r.i_stage;
   a.work = static_cast<float2*>(d_Eout);
   a.ein = static_cast<const float2*>(d_Ein);
   a.dn = static_cast<const __half*>(d_dn);

@@ -65,9 +65,9 @@ struct StepArgs {
   unsigned long long timeout_ns;
   unsigned bar_extra;
   // persistent kernel: rows and columns per CTA at most, and which per-CTA
-  // buffers live in shared memory (propagator columns, index rows, intensity rows)
+  // buffers live in shared memory (propagator columns, index rows)
   int rmax_r, rmax_c;
-  int h_res, dn_stage, i_stage;
+  int h_res, dn_stage;
 };
 
 // batched propagation (square grids): one instance's arguments
