@@ -283,6 +283,7 @@ def evaluate_volume(cs: CropSetup, seed: int, corr: "B.Corrector | None", dev, d
             B.bpm_propagate(coarse, dnc, e, e, None, 0, 1)
             corr.apply(e, dnc[0] if s.c_in == 3 else None, s.dn_scale)
             torch.mul(e.real, e.real, out=Icor[0]).addcmul_(e.imag, e.imag)
+            e = E0.clone()
             ev[4].record()
             for j in range(nzc):
                 B.bpm_propagate(coarse, dnc, e, e, None, j, j + 1)
