@@ -103,6 +103,17 @@ int bpm_coarsen_index(const void *d_dn, int nz, int ny, int nx, int factor, void
  * (FP32 activations), as training does. */
 int bpm_corrector_set_tensor_cores(bpm_corrector_t c, int on);
 
+/* Training engine of bpm_corrector_loss_grad and bpm_corrector_train_step:
+ * on != 0 computes the loss and every gradient on the tensor cores whenever
+ * w is a multiple of 128 and h even (tcgen05 kind::f16: the forward pass keeps
+ * BF16 activations; per layer the weight and bias gradients are a GEMM over
+ * the pixels with taps x input channels as rows, and the data gradient of the
+ * layer below is the adjoint convolution with the ReLU mask; BF16 operands,
+ * FP32 accumulation, FP32 master weights and Adam as before).  on = 0 (the
+ * default) trains on the FP32 pipes with FP32 activations and gradients, the
+ * path checked against the FP64 oracle to 1e-4. */
+int bpm_corrector_set_train_tensor_cores(bpm_corrector_t c, int on);
+
 /* Synchronise the stream and report a device error of the tensor-core path
  * (BPM_ERR_TIMEOUT when a bounded wait gave up). */
 int bpm_corrector_check(bpm_corrector_t c, cudaStream_t stream);

@@ -322,6 +322,7 @@ _lib.bpm_corrector_apply.argtypes = [_vp, _vp, _vp, ctypes.c_float, _i, _i, _vp]
 _lib.bpm_coarsen_index.argtypes = [_vp, _i, _i, _i, _i, _vp, _vp]
 _lib.bpm_corrector_free.argtypes = [_vp]
 _lib.bpm_corrector_set_tensor_cores.argtypes = [_vp, _i]
+_lib.bpm_corrector_set_train_tensor_cores.argtypes = [_vp, _i]
 _lib.bpm_corrector_check.argtypes = [_vp, _vp]
 _lib.bpm_corrector_last_error.restype = ctypes.c_char_p
 for _f in ("bpm_corrector_create", "bpm_corrector_param_count", "bpm_corrector_set_params",
@@ -394,6 +395,10 @@ class Corrector:
     def set_tensor_cores(self, on: bool):
         """Inference on the tensor cores (BF16 activations) or on the FP32 pipes."""
         _ccheck(_lib.bpm_corrector_set_tensor_cores(self.h, int(bool(on))))
+
+    def set_train_tensor_cores(self, on: bool):
+        """Loss and gradients on the tensor cores (BF16 operands) or on the FP32 pipes."""
+        _ccheck(_lib.bpm_corrector_set_train_tensor_cores(self.h, int(bool(on))))
 
     def check(self, stream=None):
         _ccheck(_lib.bpm_corrector_check(self.h, _stream_handle(stream)))

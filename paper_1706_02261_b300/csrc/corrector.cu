@@ -7,7 +7,8 @@
 // weights (stored as float) and accumulate in FP32.  Layout of every activation
 // tensor: [batch][channel][y][x] float; H and W multiples of 16.
 //
-// Kernels (all direct convolutions on the FP32 pipes):
+// Training kernels on the FP32 pipes (direct convolutions; the tensor-core
+// training path of bpm_corrector_set_train_tensor_cores is in namespace tc):
 //   corr_conv      forward conv (+bias, +ReLU) and, with TRANS, the adjoint
 //                  (transposed) conv of backpropagation with the ReLU mask of
 //                  the layer below fused in; one 16x16 output tile per CTA, the
@@ -457,7 +458,7 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-enum ConvOut { OUT_HIDDEN = 0, OUT_PLANES = 1, OUT_FIELD = 2 };
+enum ConvOut { OUT_HIDDEN = 0, OUT_PLANES = 1, OUT_FIELD = 2, OUT_GRAD = 3 };
 
 constexpr int kRowsTc = 2;              // output rows per tile
 
@@ -473,14 +474,20 @@ __host__ __device__ constexpr int tmem_cols(int n) { return n <= 32 ? 32 : (n <=
 //   OUT_PLANES  bias, the first cout_real channels as FP32 planes [b][c][y][x]
 //   OUT_FIELD   bias, then field[b][y][x] += sigma amp[b] (f0, f1): the
 //               residual update of the un-normalised field (apply)
+//   OUT_GRAD    no bias; each channel times (mask > 0), mask the BF16 chunk
+//               activations of the layer below: the data gradient of
+//               backpropagation with the ReLU derivative (the convolution
+//               then runs with the adjoint weights), BF16 chunks like OUT_HIDDEN
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(kThreadsTc) conv_tc(const __nv_bfloat16* __restrict__ in,
                                                       const __nv_bfloat16* __restrict__ wtc,
                                                       const float* __restrict__ bias, int cout_real,
                                                       __nv_bfloat16* __restrict__ out_bf, float* __restrict__ out_f,
                                                       float2* __restrict__ field, const float* __restrict__ amp,
-                                                      float sigma, int B, int H, int W, int* err) {
+                                                      float sigma, int B, int H, int W, int* err,
+                                                      const __nv_bfloat16* __restrict__ mask = nullptr) {
   static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 32, "padded channel counts");
+  static_assert(MODE != OUT_GRAD || COUT == 32, "gradients of the hidden layers (32 channels)");
   constexpr int R = kRowsTc;
   constexpr int KC = CIN / 8;
   constexpr int ROWB = KC * kPix * 16;            // one input row (all chunks) in shared memory
@@ -518,7 +525,7 @@ __global__ void __launch_bounds__(kThreadsTc) conv_tc(const __nv_bfloat16* __res
   }
   for (int i = threadIdx.x; i < WBYTES / 16; i += kThreadsTc)
     reinterpret_cast<uint4*>(sW)[i] = __ldg(reinterpret_cast<const uint4*>(wtc) + i);
-  if (threadIdx.x < 32) s_bias[threadIdx.x] = threadIdx.x < cout_real ? bias[threadIdx.x] : 0.f;
+  if (threadIdx.x < 32) s_bias[threadIdx.x] = (MODE != OUT_GRAD && threadIdx.x < cout_real) ? bias[threadIdx.x] : 0.f;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // weights: generic writes -> tensor-core reads
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -579,18 +586,32 @@ __global__ void __launch_bounds__(kThreadsTc) conv_tc(const __nv_bfloat16* __res
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int y = y0 + r;
-        if constexpr (MODE == OUT_HIDDEN) {
+        if constexpr (MODE == OUT_HIDDEN || MODE == OUT_GRAD) {
           float v[32];
           ld32(tmem + lanes + r * COUT, v);
 #pragma unroll
           for (int j = 0; j < COUT / 8; ++j) {
             uint32_t packed[4];
+            if constexpr (MODE == OUT_GRAD) {
+              const uint4 mk = reinterpret_cast<const uint4*>(
+                  mask + (((size_t)b * (COUT / 8) + j) * H + y) * (size_t)(W + 2) * 8)[x0 + m + 1];
+              const uint32_t mw[4] = {mk.x, mk.y, mk.z, mk.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float lo = fmaxf(v[8 * j + 2 * e] + s_bias[8 * j + 2 * e], 0.f);
-              const float hi = fmaxf(v[8 * j + 2 * e + 1] + s_bias[8 * j + 2 * e + 1], 0.f);
-              const __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
-              packed[e] = *reinterpret_cast<const uint32_t*>(&h2);
+              for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[e]);
+                const float lo = __low2float(m2) > 0.f ? v[8 * j + 2 * e] : 0.f;
+                const float hi = __high2float(m2) > 0.f ? v[8 * j + 2 * e + 1] : 0.f;
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
+                packed[e] = *reinterpret_cast<const uint32_t*>(&h2);
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float lo = fmaxf(v[8 * j + 2 * e] + s_bias[8 * j + 2 * e], 0.f);
+                const float hi = fmaxf(v[8 * j + 2 * e + 1] + s_bias[8 * j + 2 * e + 1], 0.f);
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
+                packed[e] = *reinterpret_cast<const uint32_t*>(&h2);
+              }
             }
             const uint4 q = make_uint4(packed[0], packed[1], packed[2], packed[3]);
             uint4* row = reinterpret_cast<uint4*>(out_bf + (((size_t)b * (COUT / 8) + j) * H + y) * (size_t)(W + 2) * 8);
@@ -707,6 +728,160 @@ __global__ void pack_weights(const float* __restrict__ Wl, int cin, int cout, in
   }
 }
 
+// Adjoint weights of layer W[o][c][3][3] for the data gradient: the
+// convolution from the layer's output channels (o, padded to cinp) to its
+// input channels (c, padded to coutp) with the taps mirrored,
+// out[tap][o/8][c][o%8] = W[o][c][8 - tap], zero padded.
+__global__ void pack_weights_adjoint(const float* __restrict__ Wl, int cin, int cout, int cinp, int coutp,
+                                     __nv_bfloat16* __restrict__ out) {
+  const int n = 9 * cinp * coutp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int e = i % 8, c = (i / 8) % coutp, kc = (i / (8 * coutp)) % (cinp / 8), tap = i / (8 * coutp * (cinp / 8));
+    const int o = kc * 8 + e;
+    const float w = (o < cout && c < cin) ? Wl[((size_t)o * cin + c) * 9 + (8 - tap)] : 0.f;
+    out[i] = __float2bfloat16_rn(w);
+  }
+}
+
+// Weight and bias gradients of one 3x3 layer on the tensor cores,
+//   dW[co][ci][tap] = sum_p dZ[co][p] X[ci][p + off(tap)],  db[co] = sum_p dZ[co][p],
+// as D[m][n] = sum_k A[m][k] B[n][k] with m = tap CIN + ci (and m = 9 CIN a
+// row of ones for the bias), n = co, and k running over the 128 pixels of
+// one output row segment per step (all of the CTA's segments accumulate in
+// tensor memory).  X and dZ are the BF16 chunk tensors of the forward and
+// backward passes (CIN, COUT padded channel counts).  The threads transpose
+// each segment into K-major operands in shared memory, core matrices of 8
+// rows x 8 pixels (128 bytes) laid out [row / 8][pixel / 8][row % 8][pixel %
+// 8], the x-shifted taps as their own rows; one thread issues the MMAs.  The
+// CTA writes its sums to partial[blockIdx.x][P], P = cout_real cin_real 9 +
+// cout_real, in the flat parameter order (W[co][ci][tap], then b[co]).
+constexpr int kWgradThreads = 128;
+template <int CIN, int COUT>
+struct WgradShape {
+  static constexpr int MROWS = 9 * CIN + 1;                     // taps x input channels, and the bias row
+  static constexpr int MT = (MROWS + kM - 1) / kM;              // M tiles of 128 rows
+  static constexpr int ABYTES = MT * kM * kM * 2;               // A: MT x 128 rows x 128 pixels, BF16
+  static constexpr int BBYTES = COUT * kM * 2;                  // B: COUT rows x 128 pixels
+  static constexpr int NCOL = tmem_cols(MT * COUT);
+};
+template <int CIN, int COUT>
+constexpr size_t wgrad_tc_smem() {
+  return (size_t)WgradShape<CIN, COUT>::ABYTES + WgradShape<CIN, COUT>::BBYTES + 128;
+}
+
+// element (row, pixel) of a K-major operand with 128 pixels per row
+__device__ __forceinline__ int kmaj(int row, int k) { return ((row >> 3) * (kM / 8) + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7); }
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kWgradThreads) wgrad_tc(const __nv_bfloat16* __restrict__ X,
+                                                           const __nv_bfloat16* __restrict__ dZ, int cin_real,
+                                                           int cout_real, float* __restrict__ partial, int B, int H,
+                                                           int W, int* err) {
+  using S = WgradShape<CIN, COUT>;
+  static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 32, "padded channel counts");
+  extern __shared__ __align__(128) unsigned char sm[];
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(sm);
+  __nv_bfloat16* sB = reinterpret_cast<__nv_bfloat16*>(sm + S::ABYTES);
+  __shared__ __align__(8) uint64_t bar_mma;
+  __shared__ uint32_t tmem_base;
+  const int tiles_x = W / kM, tiles = B * H * tiles_x;
+  // rows that no segment overwrites: the bias row (ones) and the padding (zeros)
+  const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+  for (int i = threadIdx.x; i < (S::MT * kM - 9 * CIN) * kM; i += kWgradThreads) {
+    const int row = 9 * CIN + i / kM, k = i % kM;
+    sA[kmaj(row, k)] = row == 9 * CIN ? one : zero;
+  }
+  if (threadIdx.x == 0) mbar_init(&bar_mma);
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                 "r"(S::NCOL)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base;
+  uint32_t ph = 0u;
+  bool ok = true;
+  int done = 0;
+  for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++done) {
+    const int tx = tile % tiles_x, y = (tile / tiles_x) % H, b = tile / (tiles_x * H);
+    const int x0 = tx * kM;
+    // A: rows tap CIN + ci, pixel k = X[ci][y + dy - 1][x0 + k + dx - 1] (padded column x0 + k + dx)
+    for (int i = threadIdx.x; i < 3 * (CIN / 8) * (kM + 2); i += kWgradThreads) {
+      const int col = i % (kM + 2), q = (i / (kM + 2)) % (CIN / 8), dy = i / ((kM + 2) * (CIN / 8));
+      const int yy = (y + dy - 1 + H) % H;
+      const uint4 v = reinterpret_cast<const uint4*>(X + (((size_t)b * (CIN / 8) + q) * H + yy) * (size_t)(W + 2) * 8)[x0 + col];
+      const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const int k = col - dx;
+        if (k < 0 || k >= kM) continue;
+        const int row0 = (dy * 3 + dx) * CIN + q * 8;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sA[kmaj(row0 + e, k)] = e8[e];
+      }
+    }
+    // B: rows co, pixel k = dZ[co][y][x0 + k]
+    for (int i = threadIdx.x; i < (COUT / 8) * kM; i += kWgradThreads) {
+      const int k = i % kM, q = i / kM;
+      const uint4 v = reinterpret_cast<const uint4*>(dZ + (((size_t)b * (COUT / 8) + q) * H + y) * (size_t)(W + 2) * 8)[x0 + k + 1];
+      const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) sB[kmaj(q * 8 + e, k)] = e8[e];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor-core reads
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      fence_after();
+      constexpr uint32_t idesc = instr_desc(kM, COUT);
+      // K-major, no swizzle: the next 8 pixels (K) one core matrix further
+      // (128 bytes), the next 8 rows (M or N) one row of core matrices further
+      const uint64_t a0 = operand_desc(saddr(sA), 128, (kM / 8) * 128);
+      const uint64_t b0 = operand_desc(saddr(sB), 128, (kM / 8) * 128);
+#pragma unroll
+      for (int t = 0; t < S::MT; ++t)
+#pragma unroll
+        for (int kb = 0; kb < kM / 16; ++kb) {
+          const uint32_t a_off = t * kM * kM * 2 + kb * 2 * 128;
+          const uint32_t b_off = kb * 2 * 128;
+          mma(tmem + t * COUT, a0 + (a_off >> 4), b0 + (b_off >> 4), idesc, done > 0 || kb > 0);
+        }
+      commit(&bar_mma);
+    }
+    ok = mbar_wait(&bar_mma, ph, err);      // the operands are free again when the MMAs have completed
+    ph ^= 1u;
+    fence_after();
+    if (__syncthreads_or(!ok)) break;
+  }
+  // read back: warp w holds rows 32w..32w+31 of each M tile
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int P = cout_real * cin_real * 9 + cout_real;
+  float* out = partial + (size_t)blockIdx.x * P;
+#pragma unroll
+  for (int t = 0; t < S::MT; ++t) {
+    float v[32];
+    if (COUT == 32) ld32(tmem + ((uint32_t)(32 * warp) << 16) + t * COUT, v);
+    else ld16(tmem + ((uint32_t)(32 * warp) << 16) + t * COUT, v);
+    const int m = t * kM + 32 * warp + lane;
+    for (int n = 0; n < cout_real; ++n) {
+      const float g = (done > 0 && ok) ? v[n] : 0.f;
+      if (m < 9 * CIN) {
+        const int tap = m / CIN, ci = m % CIN;
+        if (ci < cin_real) out[((size_t)n * cin_real + ci) * 9 + tap] = g;
+      } else if (m == 9 * CIN) {
+        out[(size_t)cout_real * cin_real * 9 + n] = g;
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::NCOL) : "memory");
+}
+
 }  // namespace tc
 
 }  // namespace
@@ -727,8 +902,13 @@ struct bpm_corrector_s {
   // tensor-core inference path
   int use_tc = 1;                  // inference on tcgen05 when the width is a multiple of 128
   __nv_bfloat16* xtc = nullptr;    // input as BF16 chunks [B][2][H][W][8]
-  __nv_bfloat16* atc[2] = {};      // hidden activations as BF16 chunks [B][4][H][W][8]
+  __nv_bfloat16* atc[3] = {};      // hidden activations as BF16 chunks [B][4][H][W][8]
   __nv_bfloat16* wtc[4] = {};      // layer weights [tap][c_in/8][c_out][8]
+  // tensor-core training path
+  int train_tc = 0;                // loss and gradients on tcgen05 when the width is a multiple of 128
+  __nv_bfloat16* gtc[2] = {};      // data gradients of the hidden layers, BF16 chunks [B][4][H][W][8]
+  __nv_bfloat16* g4tc = nullptr;   // gradient of the output layer, BF16 chunks [B][2][H][W][8]
+  __nv_bfloat16* wadj[4] = {};     // adjoint weights of layers 2..4 [tap][c_out/8][c_in][8]
   int* err = nullptr;              // device error word (bounded waits)
   unsigned wver = 1, tcver = 0;    // versions of the working weights and of their packed copy
 };
@@ -764,6 +944,11 @@ int setup_attrs() {
   rc |= set_smem(tc::conv_tc<kCh, kCh, tc::OUT_HIDDEN>, tc::conv_tc_smem<kCh, kCh>());
   rc |= set_smem(tc::conv_tc<kCh, 16, tc::OUT_PLANES>, tc::conv_tc_smem<kCh, 16>());
   rc |= set_smem(tc::conv_tc<kCh, 16, tc::OUT_FIELD>, tc::conv_tc_smem<kCh, 16>());
+  rc |= set_smem(tc::conv_tc<16, kCh, tc::OUT_GRAD>, tc::conv_tc_smem<16, kCh>());
+  rc |= set_smem(tc::conv_tc<kCh, kCh, tc::OUT_GRAD>, tc::conv_tc_smem<kCh, kCh>());
+  rc |= set_smem(tc::wgrad_tc<kCh, 16>, tc::wgrad_tc_smem<kCh, 16>());
+  rc |= set_smem(tc::wgrad_tc<kCh, kCh>, tc::wgrad_tc_smem<kCh, kCh>());
+  rc |= set_smem(tc::wgrad_tc<16, kCh>, tc::wgrad_tc_smem<16, kCh>());
   if (rc) return BPM_ERR_CUDA;
   done = true;
   return BPM_OK;
@@ -795,14 +980,18 @@ int forward(bpm_corrector_s* c, const float* x, int batch, int h, int w, cudaStr
   return BPM_OK;
 }
 
-// BF16 copy of the working weights in the tensor-core layout, refreshed when
-// the working weights have changed
+// BF16 copies of the working weights in the tensor-core layout (and the
+// adjoint weights of layers 2..4 for the data gradients), refreshed when the
+// working weights have changed
 void ensure_tc_weights(bpm_corrector_s* c, cudaStream_t s) {
   if (c->tcver == c->wver) return;
   for (int l = 0; l < 4; ++l) {
     const int n = 9 * layer_in_padded(l) * layer_out_padded(l);
     tc::pack_weights<<<(n + 255) / 256, 256, 0, s>>>(c->work + c->off[2 * l], layer_in(c, l), layer_out(l),
                                                       layer_in_padded(l), layer_out_padded(l), c->wtc[l]);
+    if (l > 0)
+      tc::pack_weights_adjoint<<<(n + 255) / 256, 256, 0, s>>>(c->work + c->off[2 * l], layer_in(c, l), layer_out(l),
+                                                                layer_out_padded(l), layer_in_padded(l), c->wadj[l]);
   }
   c->tcver = c->wver;
 }
@@ -896,6 +1085,66 @@ int loss_grad(bpm_corrector_s* c, const float* x, const float* target, int batch
   return BPM_OK;
 }
 
+// Loss and full gradient on the tensor cores: the forward pass keeps every
+// layer's BF16 chunk activations (xtc, atc[0..2]), the output layer's FP32
+// planes go through the loss kernel, then per layer from the top the weight
+// and bias gradients (wgrad_tc, summed over CTAs in a fixed order) and the
+// data gradient of the layer below (the adjoint convolution with the ReLU
+// mask, OUT_GRAD), all with BF16 operands and FP32 accumulation.
+int loss_grad_tc(bpm_corrector_s* c, const float* x, const float* target, int batch, int h, int w, cudaStream_t s) {
+  ensure_tc_weights(c, s);
+  const int hw = h * w;
+  tc::to_chunks<<<grid_for((size_t)batch * hw), 256, 0, s>>>(x, c->cin, batch, h, w, c->xtc);
+  const int grid = tc_grid(batch, h, w);
+  tc::conv_tc<16, kCh, tc::OUT_HIDDEN><<<grid, tc::kThreadsTc, tc::conv_tc_smem<16, kCh>(), s>>>(
+      c->xtc, c->wtc[0], c->work + c->off[1], kCh, c->atc[0], nullptr, nullptr, nullptr, 0.f, batch, h, w, c->err);
+  for (int l = 1; l < 3; ++l)
+    tc::conv_tc<kCh, kCh, tc::OUT_HIDDEN><<<grid, tc::kThreadsTc, tc::conv_tc_smem<kCh, kCh>(), s>>>(
+        c->atc[l - 1], c->wtc[l], c->work + c->off[2 * l + 1], kCh, c->atc[l], nullptr, nullptr, nullptr, 0.f, batch, h,
+        w, c->err);
+  tc::conv_tc<kCh, 16, tc::OUT_PLANES><<<grid, tc::kThreadsTc, tc::conv_tc_smem<kCh, 16>(), s>>>(
+      c->atc[2], c->wtc[3], c->work + c->off[7], 2, nullptr, c->z[3], nullptr, nullptr, 0.f, batch, h, w, c->err);
+  const int lblocks = 256;
+  corr_loss<<<lblocks, 256, 0, s>>>(x, c->cin, c->z[3], c->sigma, target, c->d0, c->lpart, batch, hw);
+  corr_sum<<<1, 256, 0, s>>>(c->lpart, lblocks, 1.0f / (float)((size_t)batch * 2 * hw), c->loss);
+  tc::to_chunks<<<grid_for((size_t)batch * hw), 256, 0, s>>>(c->d0, 2, batch, h, w, c->g4tc);
+  const int wtiles = batch * h * (w / tc::kM);
+  const int wgrid = std::max(1, std::min(wtiles, 148));
+  auto reduce = [&](int P, float* dst) {
+    corr_reduce<<<(P + 255) / 256, 256, 0, s>>>(c->partial, wgrid, P, dst);
+  };
+  // layer 4: gradients from A3 and dZ4; dZ3 = adjoint(dZ4) masked by A3
+  tc::wgrad_tc<kCh, 16><<<wgrid, tc::kWgradThreads, tc::wgrad_tc_smem<kCh, 16>(), s>>>(
+      c->atc[2], c->g4tc, kCh, 2, c->partial, batch, h, w, c->err);
+  reduce(2 * kCh * 9 + 2, c->grad + c->off[6]);
+  tc::conv_tc<16, kCh, tc::OUT_GRAD><<<grid, tc::kThreadsTc, tc::conv_tc_smem<16, kCh>(), s>>>(
+      c->g4tc, c->wadj[3], nullptr, kCh, c->gtc[0], nullptr, nullptr, nullptr, 0.f, batch, h, w, c->err, c->atc[2]);
+  // layers 3 and 2: gradients from A_{l-1} and dZ_l; dZ_{l-1} = adjoint(dZ_l) masked by A_{l-1}
+  int cur = 0;
+  for (int l = 2; l >= 1; --l) {
+    tc::wgrad_tc<kCh, kCh><<<wgrid, tc::kWgradThreads, tc::wgrad_tc_smem<kCh, kCh>(), s>>>(
+        c->atc[l - 1], c->gtc[cur], kCh, kCh, c->partial, batch, h, w, c->err);
+    reduce(kCh * kCh * 9 + kCh, c->grad + c->off[2 * l]);
+    tc::conv_tc<kCh, kCh, tc::OUT_GRAD><<<grid, tc::kThreadsTc, tc::conv_tc_smem<kCh, kCh>(), s>>>(
+        c->gtc[cur], c->wadj[l], nullptr, kCh, c->gtc[cur ^ 1], nullptr, nullptr, nullptr, 0.f, batch, h, w, c->err,
+        c->atc[l - 1]);
+    cur ^= 1;
+  }
+  // layer 1: gradients from the input and dZ1
+  tc::wgrad_tc<16, kCh><<<wgrid, tc::kWgradThreads, tc::wgrad_tc_smem<16, kCh>(), s>>>(
+      c->xtc, c->gtc[cur], c->cin, kCh, c->partial, batch, h, w, c->err);
+  reduce(kCh * c->cin * 9 + kCh, c->grad + c->off[0]);
+  CORR_CU(cudaGetLastError());
+  return BPM_OK;
+}
+
+// the training engine for this batch: tensor cores when enabled and the
+// width allows it, else the FP32 pipes
+int loss_grad_any(bpm_corrector_s* c, const float* x, const float* target, int batch, int h, int w, cudaStream_t s) {
+  if (c->train_tc && w % tc::kM == 0 && h % tc::kRowsTc == 0) return loss_grad_tc(c, x, target, batch, h, w, s);
+  return loss_grad(c, x, target, batch, h, w, s);
+}
+
 }  // namespace
 
 extern "C" int bpm_corrector_create(bpm_corrector_t* out, int in_channels, int max_batch, int max_h, int max_w,
@@ -923,7 +1172,8 @@ extern "C" int bpm_corrector_create(bpm_corrector_t* out, int in_channels, int m
   c->P = k;
   const size_t act = (size_t)max_batch * kCh * max_h * max_w;
   const size_t tiles = (size_t)max_batch * (max_h / kTile) * (max_w / kTile);
-  c->partial_floats = tiles * (size_t)(kCh * kCh * 9 + kCh);
+  // per-tile partials of the FP32 path, per-CTA partials of the tensor-core path (at most 148 CTAs)
+  c->partial_floats = std::max(tiles, (size_t)148) * (size_t)(kCh * kCh * 9 + kCh);
   bool ok = true;
   auto alloc = [&](float** p, size_t n) {
     if (ok && cudaMalloc(p, n * sizeof(float)) != cudaSuccess) ok = false;
@@ -952,8 +1202,11 @@ extern "C" int bpm_corrector_create(bpm_corrector_t* out, int in_channels, int m
   const size_t pad_hw = (size_t)max_h * max_w + 2 * ((size_t)max_h * max_w / 16);
   const size_t act_pad = (size_t)max_batch * kCh * pad_hw;
   alloc_bf(&c->xtc, (size_t)max_batch * 16 * pad_hw);
-  alloc_bf(&c->atc[0], act_pad);
-  alloc_bf(&c->atc[1], act_pad);
+  for (int k = 0; k < 3; ++k) alloc_bf(&c->atc[k], act_pad);
+  alloc_bf(&c->gtc[0], act_pad);
+  alloc_bf(&c->gtc[1], act_pad);
+  alloc_bf(&c->g4tc, (size_t)max_batch * 16 * pad_hw);
+  for (int l = 1; l < 4; ++l) alloc_bf(&c->wadj[l], (size_t)9 * layer_in_padded(l) * layer_out_padded(l));
   for (int l = 0; l < 4; ++l) alloc_bf(&c->wtc[l], (size_t)9 * layer_in_padded(l) * layer_out_padded(l));
   if (ok && cudaMalloc(&c->err, sizeof(int)) != cudaSuccess) ok = false;
   if (ok) cudaMemsetAsync(c->err, 0, sizeof(int), stream);
@@ -1021,7 +1274,7 @@ extern "C" int bpm_corrector_loss_grad(bpm_corrector_t c, const float* d_x, cons
   if (!c || !d_x || !d_target) return cfail(BPM_ERR_ARG, "NULL argument");
   int rc = check_dims(c, batch, h, w);
   if (rc) return rc;
-  rc = loss_grad(c, d_x, d_target, batch, h, w, stream);
+  rc = loss_grad_any(c, d_x, d_target, batch, h, w, stream);
   if (rc) return rc;
   if (h_loss) {
     CORR_CU(cudaMemcpyAsync(h_loss, c->loss, sizeof(float), cudaMemcpyDeviceToHost, stream));
@@ -1105,6 +1358,12 @@ extern "C" int bpm_corrector_set_tensor_cores(bpm_corrector_t c, int on) {
   return BPM_OK;
 }
 
+extern "C" int bpm_corrector_set_train_tensor_cores(bpm_corrector_t c, int on) {
+  if (!c) return cfail(BPM_ERR_ARG, "corrector is NULL");
+  c->train_tc = on ? 1 : 0;
+  return BPM_OK;
+}
+
 extern "C" int bpm_corrector_check(bpm_corrector_t c, cudaStream_t stream) {
   if (!c) return cfail(BPM_ERR_ARG, "corrector is NULL");
   CORR_CU(cudaStreamSynchronize(stream));
@@ -1120,9 +1379,14 @@ extern "C" int bpm_corrector_free(bpm_corrector_t c) {
                    c->a[0], c->a[1], c->a[2], c->d0, c->d1, c->partial, c->lpart, c->loss, c->outbuf, c->amp};
   for (float* b : bufs) cudaFree(b);
   cudaFree(c->xtc);
-  cudaFree(c->atc[0]);
-  cudaFree(c->atc[1]);
-  for (int l = 0; l < 4; ++l) cudaFree(c->wtc[l]);
+  for (int k = 0; k < 3; ++k) cudaFree(c->atc[k]);
+  cudaFree(c->gtc[0]);
+  cudaFree(c->gtc[1]);
+  cudaFree(c->g4tc);
+  for (int l = 0; l < 4; ++l) {
+    cudaFree(c->wtc[l]);
+    cudaFree(c->wadj[l]);
+  }
   cudaFree(c->err);
   cudaFree(c->rms_part);
   delete c;

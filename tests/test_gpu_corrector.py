@@ -148,6 +148,64 @@ def test_crop_pairs_gain_on_held_out_volumes(B, c_in, min_gain):
         corr.free()
 
 
+@pytest.mark.parametrize("c_in,bsz,h,w", [(2, 2, 32, 128), (3, 3, 16, 256)])
+def test_tensor_core_gradients_match_fp32_pipes(B, c_in, bsz, h, w):
+    """Loss and every parameter gradient from the tensor-core training path
+    (BF16 activations and data gradients, FP32 accumulation) against the FP32
+    path, which the oracle pins to 1e-4: agreement to the BF16 rounding of
+    the operands."""
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(40 + c_in)
+    theta = inputs.corrector_init(c_in, 5) + 0.05 * rng.standard_normal(inputs.corrector_param_count(c_in))
+    X = torch.from_numpy(rng.standard_normal((bsz, c_in, h, w)).astype(np.float32)).to(dev)
+    T = torch.from_numpy(rng.standard_normal((bsz, 2, h, w)).astype(np.float32)).to(dev)
+    corr = B.Corrector(c_in, 4, h, w)
+    try:
+        corr.set_residual_scale(0.37)
+        corr.set_params(theta.astype(np.float32))
+        loss32 = corr.loss_grad(X, T)
+        g32 = corr.get_params(which=2).astype(np.float64)
+        corr.set_train_tensor_cores(True)
+        loss_tc = corr.loss_grad(X, T)
+        corr.check()
+        gtc = corr.get_params(which=2).astype(np.float64)
+        print(f"c_in={c_in}: loss {loss32:.6e} / {loss_tc:.6e}")
+        assert loss_tc == pytest.approx(loss32, rel=2e-2)
+        k = 0
+        for o, i in oc.layer_shapes(c_in):
+            for size in (o * i * 9, o):
+                e = rel(gtc[k:k + size], g32[k:k + size])
+                print(f"  block {k}: rel {e:.2e}")
+                assert e <= 3e-2, (k, e)
+                k += size
+    finally:
+        corr.free()
+
+
+def test_tensor_core_training_gains_on_held_out_volumes(B):
+    """The crop recipe of the 512^3 workload at 256^3, trained on the tensor
+    cores (3 channels): the held-out field error falls as with the FP32
+    training path."""
+    from paper_1706_02261_b300 import corrector as C
+    dev = torch.device("cuda")
+    cs = C.CropSetup(n=256, nz=256, crop=128, c_in=3)
+    corr = B.Corrector(3, 32, cs.n, cs.n)
+    try:
+        corr.set_params(inputs.corrector_init(3, 0).astype(np.float32))
+        X, T = C.make_crop_pairs(cs, range(4000, 4012), corr, dev, 256, rng_seed=3)
+        corr.set_residual_scale(C.residual_scale(corr, X, T, batch=32))
+        corr.set_train_tensor_cores(True)
+        C.train(corr, X, T, steps=3000, batch=32, lr=1e-3, seed=1)
+        corr.check()
+        del X, T
+        rows = [C.evaluate_volume(cs, sd, corr, dev) for sd in range(5000, 5004)]
+        gain = np.mean([r["coarse_field"] for r in rows]) / np.mean([r["corrected_field"] for r in rows])
+        print(f"tensor-core training: field gain {gain:.2f} rows={rows}")
+        assert gain > 1.5, rows
+    finally:
+        corr.free()
+
+
 @pytest.mark.parametrize("c_in,h,w", [(2, 32, 128), (3, 16, 256)])
 def test_tensor_core_forward_matches_bf16_activation_oracle(B, c_in, h, w):
     """The tcgen05 inference engine (BF16 activations and weights, FP32
