@@ -680,17 +680,32 @@ def run_corrector(args):
         torch.cuda.synchronize(dev)
         gen_s = time.perf_counter() - t0
         corr.set_residual_scale(C.residual_scale(corr, X, T, batch=32))
+        # time of one training step (batch 32 of 128^2) on each engine, then
+        # the training itself on the tensor cores
+        step_ms = {}
+        for tc_on in (False, True):
+            corr.set_train_tensor_cores(tc_on)
+            C.train(corr, X[:32], T[:32], steps=3, batch=32, lr=1e-12, seed=0)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            C.train(corr, X, T, steps=50, batch=32, lr=1e-12, seed=0)
+            torch.cuda.synchronize(dev)
+            step_ms["tensor_cores" if tc_on else "fp32_pipes"] = (time.perf_counter() - t0) / 50 * 1e3
+        corr.set_params(inputs.corrector_init(c_in, 0).astype(np.float32))
+        corr.set_train_tensor_cores(True)
         t0 = time.perf_counter()
         losses = C.train(corr, X, T, steps=6000, batch=32, lr=1e-3, seed=1, log_every=1000)
         losses += C.train(corr, X, T, steps=2000, batch=32, lr=2.5e-4, seed=2, log_every=1000)
         torch.cuda.synchronize(dev)
+        corr.check()
         train_s = time.perf_counter() - t0
         del X, T
         rows = [C.evaluate_volume(cs, sd, corr, dev, dn_h=ph) for sd, ph in zip(held_out, test_ph)]
         corr.free()
         mean = lambda k: float(np.mean([r[k] for r in rows]))
         res[f"c_in={c_in}"] = {"pairs": 20480, "pair_generation_s": gen_s, "train_s": train_s, "train_steps": 8000,
-                               "batch": 32, "loss_trace": losses, "held_out_512": rows,
+                               "batch": 32, "train_engine": "tensor cores (tcgen05, BF16 operands)",
+                               "train_step_ms": step_ms, "loss_trace": losses, "held_out_512": rows,
                                "mean": {k: mean(k) for k in ("coarse_field", "coarse_intensity", "corrected_field",
                                                              "corrected_intensity", "fine_ms", "coarse_ms",
                                                              "corrected_ms")},
