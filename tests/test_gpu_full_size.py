@@ -137,3 +137,49 @@ def test_multiplex_1024_cubed_homogeneous_against_single_exact_step(B):
     assert ef256 <= FIELD_TOL
     assert ef <= FIELD_TOL * 1024 / 256
     assert max(errs) <= INTENSITY_TOL
+
+
+def test_batch64_workload_full_size(B):
+    """The batched workload at its full size, in the launch configuration the
+    benchmark times (one graph-captured plan of all 64 seeded instances,
+    autotuned): the three smallest instances against the oracle through their
+    whole depth, and for every instance the properties that hold at any size
+    (the slice energy never grows beyond FP32 rounding, the output field's
+    modulus squared is the last intensity plane)."""
+    ws = inputs.batch_64()
+    dev = torch.device("cuda")
+    plan = B.bpm_plan([B.Instance(w.n, w.nz, w.d, w.d, w.lam, w.n0) for w in ws], flags=B.BPM_FLAG_GRAPH)
+    try:
+        dns, eins, E0s = [], [], []
+        for k, w in enumerate(ws):
+            dns.append(torch.from_numpy(w.dn()).to(dev))
+            if w.input_kind == "plane":
+                e = torch.from_numpy(inputs.plane_wave(w.n, w.n, *w.tilt_bins)).to(dev)
+            else:
+                f = w.foci()
+                e = torch.empty((w.n, w.n), dtype=torch.complex64, device=dev)
+                B.bpm_multiplex_psf(plan, k, f.xyz_um(w.d, w.d), f.phase, f.NA, e)
+            eins.append(e)
+        eout = [torch.empty_like(e) for e in eins]
+        inten = [torch.empty((w.nz, w.n, w.n), dtype=torch.float32, device=dev) for w in ws]
+        B.bpm_autotune(plan, dns, eins, eout, inten, 32)
+        B.bpm_propagate(plan, dns, eins, eout, inten)
+        assert B.bpm_check(plan) == B.BPM_OK, B.bpm_last_error()
+        for k, w in enumerate(ws):
+            e_in = float(torch.sum(torch.abs(eins[k].to(torch.complex128)) ** 2))
+            energy = inten[k].to(torch.float64).sum(dim=(1, 2))
+            assert float(torch.max(energy[1:] - energy[:-1])) <= 1e-5 * e_in, k
+            last = (eout[k].abs() ** 2 - inten[k][-1]).abs().max() / inten[k][-1].max()
+            assert float(last) <= 1e-5, k
+        smallest = sorted(range(len(ws)), key=lambda k: ws[k].n ** 2 * ws[k].nz)[:3]
+        for k in smallest:
+            w = ws[k]
+            Er, Ir = oracle.bpm(inputs.dn_to_f64(dns[k].cpu().numpy()), eins[k].cpu().numpy(), w.d, w.d, w.d,
+                                w.lam, w.n0)
+            ef = field_rel_l2(eout[k].cpu().numpy(), Er)
+            ei = intensity_rel_max(inten[k].cpu().numpy(), Ir)
+            print(f"batch64 instance {k} ({w.n}^2 x {w.nz}): field {ef:.2e}, intensity {ei:.2e}")
+            assert ef <= FIELD_TOL * max(1.0, w.nz / 256)
+            assert ei <= INTENSITY_TOL
+    finally:
+        B.bpm_free(plan)

@@ -45,8 +45,10 @@ def test_sphere64_full(B):
     E0 = inputs.plane_wave(w.n, w.n)
     Eg, Ig = run_gpu(B, dn16, E0, w.d)
     Er, Ir = oracle.bpm(inputs.dn_to_f64(dn16), E0, w.d, w.d, w.d, w.lam, w.n0)
-    assert field_rel_l2(Eg, Er) <= FIELD_TOL
-    assert intensity_rel_max(Ig, Ir) <= INTENSITY_TOL
+    ef, ei = field_rel_l2(Eg, Er), intensity_rel_max(Ig, Ir)
+    print(f"64^3 sphere: field rel L2 {ef:.2e}, intensity max rel {ei:.2e}")
+    assert ef <= FIELD_TOL
+    assert ei <= INTENSITY_TOL
 
 
 @pytest.mark.parametrize("n", [64, 128, 192, 256, 384, 512, 1024])
@@ -102,7 +104,9 @@ def test_multiplex_synthesis_1024(B):
     finally:
         B.bpm_free(plan)
     Er = oracle.multiplex_psf(w.n, w.n, w.d, w.d, w.lam, w.n0, f.ix, f.iy, f.phase, f.zf, f.NA)
-    assert field_rel_l2(Eg, Er) <= 1e-5
+    ef = field_rel_l2(Eg, Er)
+    print(f"1024^2 multiplexed synthesis (32 x 32 foci): field rel L2 {ef:.2e}")
+    assert ef <= 1e-5
 
 
 def test_multiplex_two_depths_and_outside_emitters(B):

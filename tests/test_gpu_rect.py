@@ -144,8 +144,10 @@ def test_psf_grid_1024x2048_through_phantom(B):
         B.bpm_free(plan)
     E0 = oracle.multiplex_psf(nx, ny, d, d, 0.5, 1.33, ix, iy, ph, zf, 0.6)
     Er, Ir = oracle.bpm(inputs.dn_to_f64(dn16), E0, d, d, d, 0.5, 1.33)
-    assert field_rel_l2(Eg, Er) <= FIELD_TOL / 10
-    assert intensity_rel_max(Ig, Ir) <= INTENSITY_TOL / 10
+    ef, ei = field_rel_l2(Eg, Er), intensity_rel_max(Ig, Ir)
+    print(f"1024 x 2048 x {nz} multiplexed through the phantom: field rel L2 {ef:.2e}, intensity max rel {ei:.2e}")
+    assert ef <= FIELD_TOL / 10
+    assert ei <= INTENSITY_TOL / 10
 
 
 def test_adaptive_and_absorbing_rect(B):
