@@ -3,8 +3,9 @@
 // Plans validate problem descriptions, build the FP64 propagator tables and the
 // FFT twiddle tables on the device, and pick the team (number of CTAs that
 // share one field).  Propagation of a single field is one cooperative
-// persistent launch: the team loops over all slices with two device-wide
-// barriers per slice (see bpm_kernels.cuh); grids without a persistent kernel
+// persistent launch: the team loops over all slices, its CTAs handing the
+// field to each other twice per slice through tagged elements (see
+// bpm_kernels.cuh); grids without a persistent kernel
 // run one launch per half-step.  The kernels themselves are compiled in the
 // ops_*.cu units and found through the registry of bpm_ops.h.  Every entry
 // point returns a status code and records a message for bpm_last_error().

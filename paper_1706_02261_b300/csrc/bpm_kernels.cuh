@@ -2,7 +2,7 @@
 //
 // A "team" of CTAs owns one field of ny rows x nx columns of complex floats
 // that lives in global memory (L2-resident: 8 MiB at 1024 x 1024).  Each slice
-// of the method is two half-steps separated by team-wide barriers:
+// of the method is two half-steps, each consuming the other's output:
 //
 //   column half-step  (CTA owns a block of columns):
 //       stage its columns in shared memory, FFT_y, multiply by the propagator
@@ -15,7 +15,10 @@
 // The forward FFT_x of the first slice is a row half-step of its own.  Row
 // and column transforms run in registers (see fft.cuh) with one shared-memory
 // exchange per radix pass.  The 2D DFT needs all rows before any column, so
-// two team barriers per slice are the minimum for one field.
+// the field crosses between all CTAs twice per slice; in the persistent kernel
+// each crossing is a tagged exchange (every element carries the parity of the
+// half-step that wrote it, and consumers poll their own elements) rather than
+// a team barrier followed by the loads.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -394,6 +397,33 @@ __device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
 }
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
+// --- tagged exchange of the persistent kernel --------------------------------
+// Between the half-steps of a slice the field crosses from every CTA to every
+// other one through L2.  Instead of a team barrier before each crossing (a
+// release fence, an arrival add, a poll, then the loads: four L2 latencies in
+// a row), every element carries the parity of the half-step that wrote it in
+// the lowest mantissa bit of its real part, and each consumer polls the
+// elements it needs: row half-steps write 0, column half-steps write 1.  An
+// element is one 64-bit access (single-copy atomic), so a value with the
+// expected bit is the new value whole.  The only older value a consumer can
+// find at a location is its own write of the previous half-step (the same
+// thread reads and writes the same positions in every half-step of its kind,
+// and every half-step writes every element), which carries the other parity.
+// Nothing else crosses between CTAs during the slice loop (the propagator,
+// twiddles and index rows are read only), so no fence is needed.  Forcing the
+// bit moves the real part by at most one unit in the last place per crossing.
+__device__ __forceinline__ void st_tagged(float2* p, float2 v, unsigned tag) {
+  const unsigned long long b =
+      ((unsigned long long)__float_as_uint(v.y) << 32) | ((__float_as_uint(v.x) & ~1u) | tag);
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(b) : "memory");
+}
+__device__ __forceinline__ float2 ld_tagged(const float2* p) {
+  unsigned long long b;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(b) : "l"(p));
+  return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
+}
+__device__ __forceinline__ unsigned tag_miss(float2 v, unsigned want) { return (__float_as_uint(v.x) ^ want) & 1u; }
+
 // --- bulk asynchronous copies (TMA engine, 1D) and mbarriers ---------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -471,6 +501,43 @@ __device__ __forceinline__ bool team_barrier(const StepArgs& a, unsigned& epoch,
   return *s_flag != 0;
 }
 
+// Loads P elements of the tagged field, v[slot(i)] from ptr(slot(i)) in issue
+// order i, then reloads the ones that do not carry the tag `want` until all
+// do.  Each round trip re-reads only the missing elements.  The wait is
+// bounded like the team barrier: when timeout_ns runs out, or another CTA has
+// recorded an error, it records kDevErrTimeout (first error wins) and returns
+// false, leaving whatever was read in v (the caller finishes its half-step on
+// it, so that the CTA's barriers stay matched, and then leaves).
+template <int P, class Slot, class Ptr>
+__device__ __forceinline__ bool load_tagged(float2* v, Slot&& slot, Ptr&& ptr, unsigned want, const StepArgs& a) {
+#pragma unroll
+  for (int i = 0; i < P; ++i) {
+    const int k = slot(i);
+    v[k] = ld_tagged(ptr(k));
+  }
+  unsigned miss = 0;
+#pragma unroll
+  for (int k = 0; k < P; ++k) miss |= __float_as_uint(v[k].x) ^ want;
+  if (!(miss & 1u)) return true;
+  const unsigned long long t0 = global_timer_ns();
+  for (;;) {
+    bool again = false;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      const int k = slot(i);
+      if (tag_miss(v[k], want)) {
+        v[k] = ld_tagged(ptr(k));
+        again = true;
+      }
+    }
+    if (!again) return true;
+    if (global_timer_ns() - t0 > a.timeout_ns || ld_volatile(a.err) != 0) {
+      atomicCAS(a.err, 0, kDevErrTimeout);
+      return false;
+    }
+  }
+}
+
 // First-order correction of the propagator to slice z's mean index (reading
 // B): w[k] *= exp(i dl g(k)), k < count, with g(k) read by gk(k).  The phase
 // grows without bound towards the evanescent cut (g ~ 1 / kz0) and every
@@ -504,13 +571,32 @@ __device__ __forceinline__ void store_layout(const float2* v, float2* dst, int t
     __stcg(dst + layout_index<N, T, R>(k, t), v[k]);
   }
 }
+// ... the same layouts on the tagged field of the persistent kernel
+template <int N, int T, int R>
+__device__ __forceinline__ bool load_layout_tagged(float2* v, const float2* src, int t, unsigned want,
+                                                   const StepArgs& a) {
+  return load_tagged<N / T>(
+      v, [](int i) { return (i / R) * R + dft_input_order<R>(i % R); },
+      [&](int k) { return src + layout_index<N, T, R>(k, t); }, want, a);
+}
+template <int N, int T, int R>
+__device__ __forceinline__ void store_layout_tagged(const float2* v, float2* dst, int t, unsigned tag) {
+#pragma unroll
+  for (int i = 0; i < N / T; ++i) {
+    const int k = (i / R) * R + dft_output_order<R>(i % R);
+    st_tagged(dst + layout_index<N, T, R>(k, t), v[k], tag);
+  }
+}
 
 // Rows [r0, r1) of the team member (rows of length C::N; NYc rows in all, or
 // a.ny when NYc is 0); each group of T threads takes one row per round.
 // Groups without a row run the transforms on zeros (so that the warp or
 // group stays converged for its barriers) and skip all memory traffic.
-template <class C, int NYc, int MODE, bool KAPPA = false, bool PK = true>
-__device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1, int z, float2* s_buf,
+// TG: the working field is the persistent kernel's tagged field (rows read
+// the column half-step's tag 1 and write tag 0; the last slice's output is
+// written plain).  Returns false when a tagged wait gave up.
+template <class C, int NYc, int MODE, bool KAPPA = false, bool PK = true, bool TG = false>
+__device__ __forceinline__ bool row_half_step(const StepArgs& a, int r0, int r1, int z, float2* s_buf,
                                               const float2* s_twf, const float2* s_twi, bool& bad,
                                               const Stage& st = Stage()) {
   constexpr int N = C::N;
@@ -520,6 +606,7 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
   const int gbar = C::bar(gid);
   float2* buf = s_buf + gid * C::GS;
   const int rounds = (r1 - r0 + C::NG - 1) / C::NG;
+  bool ok = true;
   for (int k = 0; k < rounds; ++k) {
     const int row = r0 + k * C::NG + gid;
     const bool active = row < r1;
@@ -530,7 +617,10 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
 #pragma unroll
         for (int q = 0; q < C::PTS; ++q) v[q] = make_float2(0.f, 0.f);
       C::fwd(v, buf, s_twf, s_twi, t, gbar);
-      if (active) store_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
+      if (active) {
+        if constexpr (TG) store_layout_tagged<N, C::T, C::RL>(v, a.work + (size_t)row * N, t, 0u);
+        else store_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
+      }
     } else if constexpr (MODE == ROW_INV_ACC) {
       if (active) load_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
       else
@@ -548,10 +638,13 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
         }
       }
     } else {
-      if (active) load_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
-      else
+      if (active) {
+        if constexpr (TG) ok &= load_layout_tagged<N, C::T, C::RL>(v, a.work + (size_t)row * N, t, 1u, a);
+        else load_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
+      } else {
 #pragma unroll
         for (int q = 0; q < C::PTS; ++q) v[q] = make_float2(0.f, 0.f);
+      }
       // index values: from the shared-memory copy of this CTA's rows when the
       // slice was prefetched, else fetched from global memory before the
       // inverse transform so that their latency hides behind it
@@ -674,10 +767,14 @@ __device__ __forceinline__ void row_half_step(const StepArgs& a, int r0, int r1,
       } else {
         if constexpr (CJ) C::fwd_mid_fwd(v, buf, s_twf, s_twi, t, screen, gbar);
         else C::inv_mid_fwd(v, buf, s_twf, s_twi, t, screen, gbar);
-        if (active) store_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
+        if (active) {
+          if constexpr (TG) store_layout_tagged<N, C::T, C::RL>(v, a.work + (size_t)row * N, t, 0u);
+          else store_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
+        }
       }
     }
   }
+  return ok;
 }
 
 // One forward four-step transform of the columns held as in FourStepCfg:
@@ -709,8 +806,8 @@ __device__ __forceinline__ void four_step_fwd(float2* v, const float4* tw, float
 // four-step transforms (FourStepCfg): load, FFT_y, propagator H^T[col][ky],
 // inverse FFT_y (conjugated forward), store, NG columns per round, all in
 // registers apart from the two exchanges.
-template <class C, int NXc, int FLIP>
-__device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int c1, int z, float2* s_buf,
+template <class C, int NXc, int FLIP, bool TG = false>
+__device__ __forceinline__ bool col_half_step_4s(const StepArgs& a, int c0, int c1, int z, float2* s_buf,
                                                  const float2* s_tw4, const Stage& st) {
   constexpr int N = C::N;
   constexpr int N1 = C::FS_N1, NG = C::NG, SA = C::FS_SA, SC = C::FS_SC;
@@ -720,16 +817,25 @@ __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int 
   const float4* tw = reinterpret_cast<const float4*>(s_tw4) + ai;
   float2* xw = s_buf + c * SC + ai * SA;
   const float2* xr = s_buf + c * SC + ai;
+  bool ok = true;
   for (int cb = c0; cb < c1; cb += NG) {
     const int col = cb + c;
     const bool on = col < c1;
     float2 v[N1];
     {
       const float2* src = a.work + (on ? col : c0);
+      if constexpr (TG) {
+        // a column without data (past c1) reads the first column, whose
+        // elements carry the same tag
+        ok &= load_tagged<N1>(
+            v, [](int i) { return dft_input_order<N1>(i); },
+            [&](int b) { return src + (size_t)(ai + N1 * b) * nx; }, 0u, a);
+      } else {
 #pragma unroll
-      for (int i = 0; i < N1; ++i) {
-        const int b = dft_input_order<N1>(i);
-        v[b] = __ldcg(src + (size_t)(ai + N1 * b) * nx);
+        for (int i = 0; i < N1; ++i) {
+          const int b = dft_input_order<N1>(i);
+          v[b] = __ldcg(src + (size_t)(ai + N1 * b) * nx);
+        }
       }
     }
     four_step_fwd<N1, SA>(v, tw, xw, xr);
@@ -755,10 +861,12 @@ __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int 
 #pragma unroll
       for (int i = 0; i < N1; ++i) {
         const int b = dft_output_order<N1>(i);
-        __stcg(dst + (size_t)(ai + N1 * b) * nx, v[b]);
+        if constexpr (TG) st_tagged(dst + (size_t)(ai + N1 * b) * nx, v[b], 1u);
+        else __stcg(dst + (size_t)(ai + N1 * b) * nx, v[b]);
       }
     }
   }
+  return ok;
 }
 
 // Columns [c0, c1) of the team member (length C::N, row stride NXc or a.nx),
@@ -770,15 +878,17 @@ __device__ __forceinline__ void col_half_step_4s(const StepArgs& a, int c0, int 
 // half-step expects conjugated data when the row configuration is one; when
 // the two differ (a rectangular grid) FLIP conjugates the columns' output
 // (FLIP 1: always; 2: when a.flip_col is set, for the per-half-step launches).
-template <class C, int NXc, int MODE, int FLIP = 0>
-__device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1, int z, float2* s_buf,
+// TG: the persistent kernel's tagged field (columns read the row half-step's
+// tag 0 and write tag 1); returns false when a tagged wait gave up.
+template <class C, int NXc, int MODE, int FLIP = 0, bool TG = false>
+__device__ __forceinline__ bool col_half_step(const StepArgs& a, int c0, int c1, int z, float2* s_buf,
                                               const float2* s_twf, const float2* s_twi,
                                               const Stage& st = Stage()) {
   constexpr int N = C::N;
   if constexpr (C::FS_N1 > 0 && MODE == COL_PROP) {
-    col_half_step_4s<C, NXc, FLIP>(a, c0, c1, z, s_buf, s_twi + C::TWI, st);
-    return;
+    return col_half_step_4s<C, NXc, FLIP, TG>(a, c0, c1, z, s_buf, s_twi + C::TWI, st);
   }
+  bool ok = true;
   const int nx = NXc ? NXc : a.nx;
   const int gid = C::group();
   const int t = C::lane();
@@ -801,9 +911,15 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
 #pragma unroll
       for (int c = 0; c < PER; c += CHUNK) {
         float2 tmp[CHUNK];
+        if (TG && on) {
+          ok &= load_tagged<CHUNK>(
+              tmp, [](int i) { return i; }, [&](int i) { return src + (size_t)(y0 + (c + i) * YSTEP) * nx; },
+              0u, a);
+        } else {
 #pragma unroll
-        for (int i = 0; i < CHUNK; ++i)
-          tmp[i] = on ? __ldcg(src + (size_t)(y0 + (c + i) * YSTEP) * nx) : make_float2(0.f, 0.f);
+          for (int i = 0; i < CHUNK; ++i)
+            tmp[i] = on ? __ldcg(src + (size_t)(y0 + (c + i) * YSTEP) * nx) : make_float2(0.f, 0.f);
+        }
 #pragma unroll
         for (int i = 0; i < CHUNK; ++i) s_buf[cc * C::GS + C::f(y0 + (c + i) * YSTEP)] = tmp[i];
       }
@@ -879,11 +995,13 @@ __device__ __forceinline__ void col_half_step(const StepArgs& a, int c0, int c1,
 #pragma unroll 8
         for (int i = 0; i < PER; ++i) {
           const int y = y0 + i * YSTEP;
-          __stcg(dst + (size_t)y * nx, s_buf[cc * C::GS + C::f(y)]);
+          if constexpr (TG) st_tagged(dst + (size_t)y * nx, s_buf[cc * C::GS + C::f(y)], 1u);
+          else __stcg(dst + (size_t)y * nx, s_buf[cc * C::GS + C::f(y)]);
         }
       }
     }
   }
+  return ok;
 }
 
 // count twiddles from global to shared memory (ends with __syncthreads)
@@ -950,7 +1068,10 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
   load_twiddles(a.tw, s_tw, P::TW_TOTAL);    // ends with __syncthreads
   unsigned epoch = 0, dn_parity = 0;
   bool bad = false, dn_pending = false;
-  row_half_step<CR, NY, ROW_FWD>(a, lo, hi, a.z_begin, s_buf, s_twr_f, s_twr_i, bad);
+  // the entrance field's forward FFT_x writes the tagged field (tag 0); the
+  // one team barrier of the launch makes the first column half-step's reads
+  // find it (the field held the previous launch's untagged output before)
+  row_half_step<CR, NY, ROW_FWD, false, true, true>(a, lo, hi, a.z_begin, s_buf, s_twr_f, s_twr_i, bad);
   if (!team_barrier(a, epoch, &s_flag)) return;
   for (int zi = a.z_begin; zi < a.z_end; ++zi) {
     const bool last = zi + 1 == a.z_end;
@@ -963,19 +1084,19 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
       }
       dn_pending = true;
     }
-    col_half_step<CC, NX, COL_PROP, (CC::kLoop != CR::kLoop ? 1 : 0)>(a, clo, chi, z, s_buf, s_twc_f, s_twc_i,
-                                                                        st);
-    if (!team_barrier(a, epoch, &s_flag)) break;
-    bool ok = true;
+    // the half-steps exchange the field through its tags (no team barrier);
+    // a CTA barrier separates their uses of the shared buffers
+    bool ok = col_half_step<CC, NX, COL_PROP, (CC::kLoop != CR::kLoop ? 1 : 0), true>(a, clo, chi, z, s_buf,
+                                                                                      s_twc_f, s_twc_i, st);
     if (dn_pending) {
-      ok = mbar_wait_bounded(&s_mbar, dn_parity, a);
+      ok = mbar_wait_bounded(&s_mbar, dn_parity, a) && ok;
       dn_parity ^= 1u;
       dn_pending = false;
     }
     if (__syncthreads_or(!ok)) break;
-    if (!last) row_half_step<CR, NY, ROW_STEP, KAPPA>(a, lo, hi, z, s_buf, s_twr_f, s_twr_i, bad, st);
-    else row_half_step<CR, NY, ROW_LAST, KAPPA>(a, lo, hi, z, s_buf, s_twr_f, s_twr_i, bad, st);
-    if (!last && !team_barrier(a, epoch, &s_flag)) break;
+    if (!last) ok = row_half_step<CR, NY, ROW_STEP, KAPPA, true, true>(a, lo, hi, z, s_buf, s_twr_f, s_twr_i, bad, st);
+    else ok = row_half_step<CR, NY, ROW_LAST, KAPPA, true, true>(a, lo, hi, z, s_buf, s_twr_f, s_twr_i, bad, st);
+    if (__syncthreads_or(!ok)) break;
   }
   // leave no copy in flight: a prefetch abandoned by a failed barrier is
   // waited for (bounded)
