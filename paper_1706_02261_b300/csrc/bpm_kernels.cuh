@@ -422,7 +422,6 @@ __device__ __forceinline__ float2 ld_tagged(const float2* p) {
   asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(b) : "l"(p));
   return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
 }
-__device__ __forceinline__ unsigned tag_miss(float2 v, unsigned want) { return (__float_as_uint(v.x) ^ want) & 1u; }
 
 // --- bulk asynchronous copies (TMA engine, 1D) and mbarriers ---------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -508,24 +507,26 @@ __device__ __forceinline__ bool team_barrier(const StepArgs& a, unsigned& epoch,
 // recorded an error, it records kDevErrTimeout (first error wins) and returns
 // false, leaving whatever was read in v (the caller finishes its half-step on
 // it, so that the CTA's barriers stay matched, and then leaves).
-template <int P, class Slot, class Ptr>
-__device__ __forceinline__ bool load_tagged(float2* v, Slot&& slot, Ptr&& ptr, unsigned want, const StepArgs& a) {
+template <unsigned WANT, int P, class Slot, class Ptr>
+__device__ __forceinline__ bool load_tagged(float2* v, Slot&& slot, Ptr&& ptr, const StepArgs& a) {
 #pragma unroll
   for (int i = 0; i < P; ++i) {
     const int k = slot(i);
     v[k] = ld_tagged(ptr(k));
   }
-  unsigned miss = 0;
+  // all tags equal to WANT: the AND of the words has the bit (WANT 1), or
+  // their OR lacks it (WANT 0); three-input logic folds two words per step
+  unsigned acc = WANT ? ~0u : 0u;
 #pragma unroll
-  for (int k = 0; k < P; ++k) miss |= __float_as_uint(v[k].x) ^ want;
-  if (!(miss & 1u)) return true;
+  for (int k = 0; k < P; ++k) acc = WANT ? (acc & __float_as_uint(v[k].x)) : (acc | __float_as_uint(v[k].x));
+  if ((acc & 1u) == WANT) return true;
   const unsigned long long t0 = global_timer_ns();
   for (;;) {
     bool again = false;
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       const int k = slot(i);
-      if (tag_miss(v[k], want)) {
+      if ((__float_as_uint(v[k].x) & 1u) != WANT) {
         v[k] = ld_tagged(ptr(k));
         again = true;
       }
@@ -572,12 +573,11 @@ __device__ __forceinline__ void store_layout(const float2* v, float2* dst, int t
   }
 }
 // ... the same layouts on the tagged field of the persistent kernel
-template <int N, int T, int R>
-__device__ __forceinline__ bool load_layout_tagged(float2* v, const float2* src, int t, unsigned want,
-                                                   const StepArgs& a) {
-  return load_tagged<N / T>(
+template <unsigned WANT, int N, int T, int R>
+__device__ __forceinline__ bool load_layout_tagged(float2* v, const float2* src, int t, const StepArgs& a) {
+  return load_tagged<WANT, N / T>(
       v, [](int i) { return (i / R) * R + dft_input_order<R>(i % R); },
-      [&](int k) { return src + layout_index<N, T, R>(k, t); }, want, a);
+      [&](int k) { return src + layout_index<N, T, R>(k, t); }, a);
 }
 template <int N, int T, int R>
 __device__ __forceinline__ void store_layout_tagged(const float2* v, float2* dst, int t, unsigned tag) {
@@ -639,7 +639,7 @@ __device__ __forceinline__ bool row_half_step(const StepArgs& a, int r0, int r1,
       }
     } else {
       if (active) {
-        if constexpr (TG) ok &= load_layout_tagged<N, C::T, C::RL>(v, a.work + (size_t)row * N, t, 1u, a);
+        if constexpr (TG) ok &= load_layout_tagged<1u, N, C::T, C::RL>(v, a.work + (size_t)row * N, t, a);
         else load_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
       } else {
 #pragma unroll
@@ -827,9 +827,9 @@ __device__ __forceinline__ bool col_half_step_4s(const StepArgs& a, int c0, int 
       if constexpr (TG) {
         // a column without data (past c1) reads the first column, whose
         // elements carry the same tag
-        ok &= load_tagged<N1>(
+        ok &= load_tagged<0u, N1>(
             v, [](int i) { return dft_input_order<N1>(i); },
-            [&](int b) { return src + (size_t)(ai + N1 * b) * nx; }, 0u, a);
+            [&](int b) { return src + (size_t)(ai + N1 * b) * nx; }, a);
       } else {
 #pragma unroll
         for (int i = 0; i < N1; ++i) {
@@ -912,9 +912,8 @@ __device__ __forceinline__ bool col_half_step(const StepArgs& a, int c0, int c1,
       for (int c = 0; c < PER; c += CHUNK) {
         float2 tmp[CHUNK];
         if (TG && on) {
-          ok &= load_tagged<CHUNK>(
-              tmp, [](int i) { return i; }, [&](int i) { return src + (size_t)(y0 + (c + i) * YSTEP) * nx; },
-              0u, a);
+          ok &= load_tagged<0u, CHUNK>(
+              tmp, [](int i) { return i; }, [&](int i) { return src + (size_t)(y0 + (c + i) * YSTEP) * nx; }, a);
         } else {
 #pragma unroll
           for (int i = 0; i < CHUNK; ++i)
