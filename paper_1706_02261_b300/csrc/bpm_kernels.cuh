@@ -32,9 +32,10 @@
 namespace bpmk {
 
 // Per-length transform configuration.  Two engines:
-//  - LoopCfg: N = R^P with one radix R; a rolled pass loop (LoopFFT) and the
-//    inverse by conjugation, so a half-step is one compact loop over 2P passes
-//    with the pointwise operation (propagator or screen) in the middle.
+//  - LoopCfg: N = R^P with one radix R; one pass function (LoopFFT) and the
+//    inverse by conjugation, so a half-step is a loop over 2P passes with the
+//    pointwise operation (propagator or screen) in the middle, rolled (one
+//    compact copy of the pass) or unrolled (U, the 1024-point transform).
 //  - GroupCfg: mixed radices (products with 3, or 2^7) through the unrolled
 //    GroupFFT with separate forward and inverse schedules.
 // Both expose: T threads per row, the register layouts L(R0) (natural order,
@@ -60,9 +61,9 @@ struct CfgBase {
   __device__ __forceinline__ static int bar(int gid) { return T_ > 32 ? 1 + gid : 0; }
 };
 
-template <int N_, int T_, int R_, int PAD_, int GS_>
+template <int N_, int T_, int R_, int PAD_, int GS_, bool U_ = false>
 struct LoopCfg : CfgBase<N_, T_, GS_> {
-  using E = LoopFFT<N_, T_, R_, PAD_>;
+  using E = LoopFFT<N_, T_, R_, PAD_, U_>;
   static constexpr bool kLoop = true;
   static constexpr int R0 = R_, RL = R_;
   static constexpr int TWF = E::TW, TWI = 0;
@@ -76,32 +77,30 @@ struct LoopCfg : CfgBase<N_, T_, GS_> {
                                              int bar = 0) {
     E::run_inv(v, buf, twf, t, bar);
   }
-  // inverse, mid(v) on natural-order data, forward: one rolled loop
+  // inverse, mid(v) on natural-order data, forward: one pass loop
   template <class Mid>
   __device__ __forceinline__ static void inv_mid_fwd(float2* v, float2* buf, const float2* twf,
                                                      const float2*, int t, Mid&& mid, int bar = 0) {
     conj_all(v, E::PTS);
-#pragma unroll 1
-    for (int q = 0; q < 2 * E::NP; ++q) {
+    pass_loop<U_, 2 * E::NP>([&](int q) {
       if (q == E::NP) {
         conj_all(v, E::PTS);
         mid(v);
       }
       E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t, bar);
-    }
+    });
   }
-  // forward, mid(v) on spectrum-order data, inverse: one rolled loop
+  // forward, mid(v) on spectrum-order data, inverse: one pass loop
   template <class Mid>
   __device__ __forceinline__ static void fwd_mid_inv(float2* v, float2* buf, const float2* twf,
                                                      const float2*, int t, Mid&& mid, int bar = 0) {
-#pragma unroll 1
-    for (int q = 0; q < 2 * E::NP; ++q) {
+    pass_loop<U_, 2 * E::NP>([&](int q) {
       if (q == E::NP) {
         mid(v);
         conj_all(v, E::PTS);
       }
       E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t, bar);
-    }
+    });
     conj_all(v, E::PTS);
   }
   // The propagation step's hand-off from the column to the row half-step
@@ -115,11 +114,10 @@ struct LoopCfg : CfgBase<N_, T_, GS_> {
   template <class Mid>
   __device__ __forceinline__ static void fwd_mid_fwd(float2* v, float2* buf, const float2* twf,
                                                      const float2*, int t, Mid&& mid, int bar = 0) {
-#pragma unroll 1
-    for (int q = 0; q < 2 * E::NP; ++q) {
+    pass_loop<U_, 2 * E::NP>([&](int q) {
       if (q == E::NP) mid(v);
       E::pass(q < E::NP ? q : q - E::NP, v, buf, twf, t, bar);
-    }
+    });
   }
   // conjugated data in, conjugate of the inverse out
   __device__ __forceinline__ static void inv_c(float2* v, float2* buf, const float2* twf, const float2*, int t,
@@ -217,7 +215,7 @@ template <> struct Cfg<256> : GroupCfg<256, 32, 274, GroupFFT<256, 32, 16, -1, R
 template <> struct Cfg<384> : GroupCfg<384, 16, 409, GroupFFT<384, 16, 16, -1, Rad8x8x6>, GroupFFT<384, 16, 16, +1, Rad6x8x8>> {};
 template <> struct Cfg<512> : LoopCfg<512, 32, 8, 16, 546> {};
 template <> struct Cfg<768> : GroupCfg<768, 32, 818, GroupFFT<768, 32, 16, -1, Radices<8, 8, 12>>, GroupFFT<768, 32, 16, +1, Radices<12, 8, 8>>> {};
-template <> struct Cfg<1024> : FourStepCfg<LoopCfg<1024, 32, 32, 32, 1058>, 32> {};
+template <> struct Cfg<1024> : FourStepCfg<LoopCfg<1024, 32, 32, 32, 1058, true>, 32> {};
 // 1536 and 2048: two warps per row or column (64 threads, 24 or 32 points
 // each), synchronised by a named barrier per group
 template <> struct Cfg<1536> : GroupCfg<1536, 64, 1634, GroupFFT<1536, 64, 16, -1, Radices<8, 8, 24>>, GroupFFT<1536, 64, 16, +1, Radices<24, 8, 8>>> {};
@@ -234,7 +232,7 @@ template <> struct Cfg<512, 2> : GroupCfg<512, 32, 546, GroupFFT<512, 32, 16, -1
                                           GroupFFT<512, 32, 16, +1, Radices<2, 16, 16>>> {};
 template <> struct Cfg<256, 1> : GroupCfg<256, 32, 274, GroupFFT<256, 32, 16, -1, Rad4x8x8>, GroupFFT<256, 32, 16, +1, Rad8x8x4>> {};
 template <> struct Cfg<256, 2> : LoopCfg<256, 16, 16, 16, 273> {};
-template <> struct Cfg<1024, 1> : LoopCfg<1024, 32, 32, 32, 1058> {};
+template <> struct Cfg<1024, 1> : LoopCfg<1024, 32, 32, 32, 1058, true> {};
 
 // number of schedules of length n (Cfg<n, 0> .. Cfg<n, kSchedules(n) - 1>)
 __host__ __device__ constexpr int kSchedules(int n) { return n == 256 || n == 512 ? 3 : (n == 1024 ? 2 : 1); }
