@@ -331,6 +331,17 @@ int bpm_set_schedule(bpm_plan_t p, int schedule);
 int bpm_debug_set_barrier_timeout(bpm_plan_t p, unsigned long long timeout_ns,
                                   unsigned extra_arrivals);
 
+/* bpm_debug_stall_exchange - test hook for the bounded wait of the field
+ * exchange between the half-steps of a single-field persistent launch (each
+ * element carries the parity of the half-step that wrote it; consumers poll
+ * their elements).  With on != 0 the entrance field's forward transform
+ * writes the parity the row half-steps write later, so the first column
+ * half-step waits for a value that never comes: the wait runs out after the
+ * plan's limit (bpm_debug_set_barrier_timeout), records BPM_ERR_TIMEOUT and
+ * every CTA leaves the kernel, leaving the context usable.  0 in normal use;
+ * plans without a persistent kernel ignore it.  Errors: BPM_ERR_ARG. */
+int bpm_debug_stall_exchange(bpm_plan_t p, int on);
+
 #ifdef __cplusplus
 }
 #endif

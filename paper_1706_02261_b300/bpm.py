@@ -67,6 +67,7 @@ _lib.bpm_free.argtypes = [_vp]
 _lib.bpm_last_error.restype = ctypes.c_char_p
 _lib.bpm_plan_info.argtypes = [_vp, ctypes.POINTER(_i), _i]
 _lib.bpm_debug_set_barrier_timeout.argtypes = [_vp, ctypes.c_ulonglong, _u]
+_lib.bpm_debug_stall_exchange.argtypes = [_vp, _i]
 _lib.bpm_autotune.argtypes = [_vp, _pp, _pp, _pp, _pp, _i, _vp]
 _lib.bpm_set_schedule.argtypes = [_vp, _i]
 _lib.bpm_propagate_host.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _i, _vp]
@@ -77,7 +78,7 @@ _lib.bpm_phase_conjugate.argtypes = [_vp, _i, _vp, _vp]
 _lib.bpm_propagate_absorbing.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp]
 _lib.bpm_demultiplex.argtypes = [_vp, _i, _vp, _i, _i, _i, ctypes.POINTER(_i), _i, _i, _i, _vp, _vp]
 for _f in ("bpm_plan", "bpm_propagate", "bpm_multiplex_psf", "bpm_light_sheet", "bpm_check",
-           "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout", "bpm_propagate_static", "bpm_autotune", "bpm_propagate_host",
+           "bpm_free", "bpm_plan_info", "bpm_debug_set_barrier_timeout", "bpm_debug_stall_exchange", "bpm_propagate_static", "bpm_autotune", "bpm_propagate_host",
            "bpm_set_schedule"):
     getattr(_lib, _f).restype = _i
 
@@ -295,6 +296,10 @@ def bpm_set_schedule(plan, schedule: int) -> int:
 
 def bpm_debug_set_barrier_timeout(plan, timeout_ns: int, extra_arrivals: int = 0) -> int:
     return _check(_lib.bpm_debug_set_barrier_timeout(plan, timeout_ns, extra_arrivals))
+
+
+def bpm_debug_stall_exchange(plan, on: bool) -> int:
+    return _check(_lib.bpm_debug_stall_exchange(plan, 1 if on else 0))
 
 
 def bpm_propagate_static(instance: "Instance", dn, e_in, e_out, inten=None, z_begin: int = 0,

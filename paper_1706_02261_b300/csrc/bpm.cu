@@ -161,6 +161,7 @@ struct bpm_plan_s {
   int foci_cap = 0;
   unsigned long long timeout_ns = 2000000000ull;
   unsigned bar_extra = 0;
+  int tag_stall = 0;                // test hook (bpm_debug_stall_exchange)
   cudaStream_t last = 0;
   // batched plans (n_inst > 1): one persistent cluster launch
   InstArgs* d_inst = nullptr;
@@ -400,6 +401,7 @@ StepArgs base_args(bpm_plan_s* p, const InstPlan& in) {
   a.err = p->err;
   a.timeout_ns = p->timeout_ns;
   a.bar_extra = p->bar_extra;
+  a.tag_stall = p->tag_stall;
   a.carrier = make_float2(1.f, 0.f);
   return a;
 }
@@ -1296,6 +1298,12 @@ extern "C" int bpm_debug_set_barrier_timeout(bpm_plan_t p, unsigned long long ti
   if (timeout_ns == 0) return fail(BPM_ERR_ARG, "timeout must be positive");
   p->timeout_ns = timeout_ns;
   p->bar_extra = extra;
+  return BPM_OK;
+}
+
+extern "C" int bpm_debug_stall_exchange(bpm_plan_t p, int on) {
+  if (!p) return fail(BPM_ERR_ARG, "plan is NULL");
+  p->tag_stall = on ? 1 : 0;
   return BPM_OK;
 }
 

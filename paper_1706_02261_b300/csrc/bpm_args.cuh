@@ -64,6 +64,9 @@ struct StepArgs {
   int* err;
   unsigned long long timeout_ns;
   unsigned bar_extra;
+  // test hook: the entrance field's forward transform writes the tag the row
+  // half-steps write (1 instead of 0), so the first tagged wait runs out
+  int tag_stall;
   // persistent kernel: rows and columns per CTA at most, and which per-CTA
   // buffers live in shared memory (propagator columns, index rows)
   int rmax_r, rmax_c;

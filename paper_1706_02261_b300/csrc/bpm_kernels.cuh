@@ -632,7 +632,7 @@ __device__ __forceinline__ bool row_half_step(const StepArgs& a, int r0, int r1,
         for (int q = 0; q < C::PTS; ++q) v[q] = make_float2(0.f, 0.f);
       C::fwd(v, buf, s_twf, s_twi, t, gbar);
       if (active) {
-        if constexpr (TG) store_layout_tagged<N, C::T, C::RL>(v, a.work + (size_t)row * N, t, 0u);
+        if constexpr (TG) store_layout_tagged<N, C::T, C::RL>(v, a.work + (size_t)row * N, t, a.tag_stall ? 1u : 0u);
         else store_layout<N, C::T, C::RL>(v, a.work + (size_t)row * N, t);
       }
     } else if constexpr (MODE == ROW_INV_ACC) {

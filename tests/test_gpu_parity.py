@@ -208,6 +208,38 @@ def test_barrier_timeout_is_reported_and_context_survives(B):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("n", [256, 1024])
+def test_exchange_timeout_is_reported_and_context_survives(B, n):
+    # The entrance field carries the parity the row half-steps write, so the
+    # first column half-step polls for elements that never arrive; the bounded
+    # wait runs out after 2 ms, every CTA leaves the kernel and the status says
+    # so.  The same plan then propagates correctly.
+    nz, d = 4, 0.1
+    dev = torch.device("cuda")
+    plan = B.bpm_plan(B.Instance(n, nz, d, d))
+    try:
+        assert B.bpm_plan_info(plan)["persistent"] == 1
+        rng = np.random.default_rng(n)
+        dn16 = rng.uniform(0.0, 0.05, size=(nz, n, n)).astype(np.float16)
+        dn_t = torch.from_numpy(dn16).to(dev)
+        E0 = bandlimited_field(n, d, 0.9, n + 1)
+        e = torch.from_numpy(np.ascontiguousarray(E0, np.complex64)).to(dev)
+        out = torch.empty_like(e)
+        B.bpm_debug_set_barrier_timeout(plan, 2_000_000, 0)
+        B.bpm_debug_stall_exchange(plan, True)
+        B.bpm_propagate(plan, dn_t, e, out, None)
+        assert B.bpm_check(plan) == B.BPM_ERR_TIMEOUT
+        B.bpm_debug_stall_exchange(plan, False)
+        B.bpm_debug_set_barrier_timeout(plan, 2_000_000_000, 0)
+        B.bpm_propagate(plan, dn_t, e, out, None)
+        assert B.bpm_check(plan) == B.BPM_OK
+        Er, _ = oracle.bpm(inputs.dn_to_f64(dn16), E0, d, d, d, 0.5, 1.33)
+        assert field_rel_l2(out.cpu().numpy(), Er) <= FIELD_TOL / 10
+    finally:
+        B.bpm_free(plan)
+    torch.cuda.synchronize()
+
+
 def test_argument_errors(B):
     dev = torch.device("cuda")
     with pytest.raises(B.BpmError) as ei:
