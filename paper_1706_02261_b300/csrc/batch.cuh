@@ -33,13 +33,13 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_batch_kernel(BatchArgs b) {
     if (k >= b.n_inst) break;
     const InstArgs ia = b.inst[b.order[k]];
     switch (ia.n) {
-      case 64: batch_instance<Cfg<64>>(ia, b.err, rank, CL, smem, bad); break;
-      case 128: batch_instance<Cfg<128>>(ia, b.err, rank, CL, smem, bad); break;
-      case 192: batch_instance<Cfg<192>>(ia, b.err, rank, CL, smem, bad); break;
-      case 256: batch_instance<Cfg<256, SS::s256>>(ia, b.err, rank, CL, smem, bad); break;
-      case 384: batch_instance<Cfg<384>>(ia, b.err, rank, CL, smem, bad); break;
-      case 512: batch_instance<Cfg<512, SS::s512>>(ia, b.err, rank, CL, smem, bad); break;
-      case 1024: batch_instance<Cfg<1024, SS::s1024>>(ia, b.err, rank, CL, smem, bad); break;
+      case 64: batch_instance<Cfg<64>>(ia, b, rank, CL, smem, bad); break;
+      case 128: batch_instance<Cfg<128>>(ia, b, rank, CL, smem, bad); break;
+      case 192: batch_instance<Cfg<192>>(ia, b, rank, CL, smem, bad); break;
+      case 256: batch_instance<Cfg<256, SS::s256>>(ia, b, rank, CL, smem, bad); break;
+      case 384: batch_instance<Cfg<384>>(ia, b, rank, CL, smem, bad); break;
+      case 512: batch_instance<Cfg<512, SS::s512>>(ia, b, rank, CL, smem, bad); break;
+      case 1024: batch_instance<Cfg<1024, SS::s1024>>(ia, b, rank, CL, smem, bad); break;
       default: break;
     }
   }

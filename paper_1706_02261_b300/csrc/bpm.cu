@@ -602,6 +602,7 @@ int enqueue_batch(bpm_plan_s* p, int clusters, cudaStream_t s) {
   b.from_back = 0;
   b.back_min = 0;
   b.err = p->err;
+  b.timeout_ns = p->timeout_ns;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -97,6 +97,7 @@ struct BatchArgs {
   int from_back;                // 0: take from the front (largest first); 1: from the back (smallest first)
   int back_min;                 // a back taker takes no position below this (too large for its team)
   int* err;
+  unsigned long long timeout_ns;  // limit of every device wait (tagged exchange, queue)
 };
 
 // Position of the twiddle of butterfly b, radix element r, thread t within

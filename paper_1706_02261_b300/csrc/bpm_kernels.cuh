@@ -1229,10 +1229,13 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_light_sheet_kernel(StepArgs a
 // ---------------------------------------------------------------------------
 // Every thread-block cluster is a team: it takes the next instance from a
 // device work queue (instances are queued largest first), runs all of that
-// instance's slices with the cluster's hardware barrier between half-steps
-// (release/acquire at cluster scope, so the field exchanged through L2 is
-// visible), then takes the next one.  No grid-wide barrier is involved, so
-// clusters run independently and instances of different sizes mix freely.
+// instance's slices, its CTAs handing the field to each other through L2
+// (by the tagged exchange of the persistent kernel for small sizes, the
+// cluster's CTAs being resident together, else with the cluster's hardware
+// barrier between half-steps, release/acquire at cluster scope), then takes
+// the next one.  No grid-wide
+// barrier is involved, so clusters run independently and instances of
+// different sizes mix freely.
 
 // One queue position for a team (its leader thread): the main launch takes
 // positions from the front of the order, a fill launch of smaller teams (on
@@ -1281,8 +1284,8 @@ __device__ __forceinline__ unsigned cluster_id() {
 }
 
 template <class C>
-__device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int rank, int CL, float2* smem,
-                                               bool& bad) {
+__device__ __forceinline__ void batch_instance(const InstArgs& ia, const BatchArgs& b, int rank, int CL,
+                                               float2* smem, bool& bad) {
   constexpr int N = C::N;
   float2* s_twf = smem;
   float2* s_twi = s_twf + C::TWF;
@@ -1302,7 +1305,8 @@ __device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int
   a.carrier = ia.carrier;
   a.z_begin = ia.z_begin;
   a.z_end = ia.z_end;
-  a.err = err;
+  a.err = b.err;
+  a.timeout_ns = b.timeout_ns;
   a.accumulate = 0;
   a.out = nullptr;
   const int lo = (rank * N) / CL, hi = ((rank + 1) * N) / CL;
@@ -1314,14 +1318,32 @@ __device__ __forceinline__ void batch_instance(const InstArgs& ia, int* err, int
     return;
   }
   load_twiddles(a.tw, s_twf, cfg_twiddles<C>());
-  row_half_step<C, N, ROW_FWD>(a, lo, hi, a.z_begin, s_buf, s_twf, s_twi, bad);
+  // Small sizes hand the field between their half-steps through tagged
+  // elements (as the persistent kernel does): the cluster barrier after the
+  // entrance field's forward FFT_x makes its tagged writes visible, a CTA
+  // barrier separates the half-steps' uses of shared memory, and a failed
+  // wait ends the instance for this CTA (the others' waits give up on the
+  // error word).  Their slices are short (a 128^2 slice on 8 CTAs: 7.5 ->
+  // 6.4 us).  From 256 on, each CTA takes several rounds of rows or columns
+  // per half-step and the cluster's hardware barrier costs less than the
+  // polls (512^2: 54 us with the barrier, 58 us tagged).
+  constexpr bool TGB = N <= 192;
+  row_half_step<C, N, ROW_FWD, false, true, TGB>(a, lo, hi, a.z_begin, s_buf, s_twf, s_twi, bad);
   cluster_sync_all();
   for (int z = a.z_begin; z < a.z_end; ++z) {
-    col_half_step<C, N, COL_PROP>(a, lo, hi, z, s_buf, s_twf, s_twi);
-    cluster_sync_all();
-    if (z + 1 < a.z_end) row_half_step<C, N, ROW_STEP, false, false>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
-    else row_half_step<C, N, ROW_LAST, false, false>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
-    cluster_sync_all();
+    bool ok = col_half_step<C, N, COL_PROP, 0, TGB>(a, lo, hi, z, s_buf, s_twf, s_twi);
+    if constexpr (TGB) {
+      if (__syncthreads_or(!ok)) break;
+    } else {
+      cluster_sync_all();
+    }
+    if (z + 1 < a.z_end) ok = row_half_step<C, N, ROW_STEP, false, false, TGB>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+    else ok = row_half_step<C, N, ROW_LAST, false, false, TGB>(a, lo, hi, z, s_buf, s_twf, s_twi, bad);
+    if constexpr (TGB) {
+      if (__syncthreads_or(!ok)) break;
+    } else {
+      cluster_sync_all();
+    }
   }
 }
 
