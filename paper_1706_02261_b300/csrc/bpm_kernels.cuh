@@ -1115,7 +1115,7 @@ __global__ void __launch_bounds__(kThreads, 1) bpm_persistent_kernel(StepArgs a)
     else ok = row_half_step<CR, NY, ROW_LAST, KAPPA, true, true>(a, lo, hi, z, s_buf, s_twr_f, s_twr_i, bad, st);
     if (__syncthreads_or(!ok)) break;
   }
-  // leave no copy in flight: a prefetch abandoned by a failed barrier is
+  // leave no copy in flight: a prefetch abandoned by a failed wait is
   // waited for (bounded)
   if (dn_pending) mbar_wait_bounded(&s_mbar, dn_parity, a);
   report_bad(a, bad);
