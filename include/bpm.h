@@ -338,8 +338,12 @@ int bpm_debug_set_barrier_timeout(bpm_plan_t p, unsigned long long timeout_ns,
  * writes the parity the row half-steps write later, so the first column
  * half-step waits for a value that never comes: the wait runs out after the
  * plan's limit (bpm_debug_set_barrier_timeout), records BPM_ERR_TIMEOUT and
- * every CTA leaves the kernel, leaving the context usable.  0 in normal use;
- * plans without a persistent kernel ignore it.  Errors: BPM_ERR_ARG. */
+ * every CTA leaves the kernel, leaving the context usable.  Batched plans:
+ * the same for their instances that use the exchange (sides up to 192); the
+ * setting is read when the batched launch is made, so plans with
+ * BPM_FLAG_GRAPH keep the value their graph was captured with.  0 in normal
+ * use; plans that run one launch per half-step ignore it.  Errors:
+ * BPM_ERR_ARG. */
 int bpm_debug_stall_exchange(bpm_plan_t p, int on);
 
 #ifdef __cplusplus

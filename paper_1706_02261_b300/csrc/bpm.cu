@@ -603,6 +603,7 @@ int enqueue_batch(bpm_plan_s* p, int clusters, cudaStream_t s) {
   b.back_min = 0;
   b.err = p->err;
   b.timeout_ns = p->timeout_ns;
+  b.tag_stall = p->tag_stall;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -98,6 +98,7 @@ struct BatchArgs {
   int back_min;                 // a back taker takes no position below this (too large for its team)
   int* err;
   unsigned long long timeout_ns;  // limit of every device wait (tagged exchange, queue)
+  int tag_stall;                  // test hook, as StepArgs::tag_stall (tagged instance sizes)
 };
 
 // Position of the twiddle of butterfly b, radix element r, thread t within

@@ -1307,6 +1307,7 @@ __device__ __forceinline__ void batch_instance(const InstArgs& ia, const BatchAr
   a.z_end = ia.z_end;
   a.err = b.err;
   a.timeout_ns = b.timeout_ns;
+  a.tag_stall = b.tag_stall;
   a.accumulate = 0;
   a.out = nullptr;
   const int lo = (rank * N) / CL, hi = ((rank + 1) * N) / CL;

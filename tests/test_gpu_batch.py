@@ -184,3 +184,36 @@ def test_batch_every_instance_exactly_once_with_fill_teams(B):
                 assert field_rel_l2(eg.cpu().numpy(), Er) <= FIELD_TOL / 10, (n, rep)
     finally:
         B.bpm_free(plan)
+
+
+def test_batched_exchange_timeout_is_reported_and_context_survives(B):
+    # Small instances hand the field between half-steps through tagged
+    # elements; with the entrance field carrying the wrong parity their waits
+    # run out after 2 ms, the batch reports BPM_ERR_TIMEOUT, and the same plan
+    # then propagates correctly (a larger instance, on the cluster barrier,
+    # rides along).
+    cases = []
+    for k, (n, nz) in enumerate([(128, 4), (192, 3), (256, 3), (64, 4)]):
+        rng = np.random.default_rng(300 + k)
+        dn16 = rng.uniform(0, 0.05, size=(nz, n, n)).astype(np.float16)
+        cases.append((n, nz, 0.1, dn16, bandlimited_field(n, 0.1, 0.85, 400 + k)))
+    dev = torch.device("cuda")
+    plan = B.bpm_plan([B.Instance(n, nz, d, d) for (n, nz, d, _, _) in cases])
+    try:
+        dn = [torch.from_numpy(c[3]).to(dev) for c in cases]
+        ein = [torch.from_numpy(c[4]).to(dev) for c in cases]
+        eout = [torch.empty_like(e) for e in ein]
+        B.bpm_debug_set_barrier_timeout(plan, 2_000_000, 0)
+        B.bpm_debug_stall_exchange(plan, True)
+        B.bpm_propagate(plan, dn, ein, eout, None)
+        assert B.bpm_check(plan) == B.BPM_ERR_TIMEOUT
+        B.bpm_debug_stall_exchange(plan, False)
+        B.bpm_debug_set_barrier_timeout(plan, 2_000_000_000, 0)
+        B.bpm_propagate(plan, dn, ein, eout, None)
+        assert B.bpm_check(plan) == B.BPM_OK, B.bpm_last_error()
+        for (n, nz, d, dn16, E0), e in zip(cases, eout):
+            Er, _ = oracle.bpm(inputs.dn_to_f64(dn16), E0, d, d, d, 0.5, 1.33)
+            assert field_rel_l2(e.cpu().numpy(), Er) <= FIELD_TOL / 10
+    finally:
+        B.bpm_free(plan)
+    torch.cuda.synchronize()
