@@ -593,7 +593,8 @@ def run_batch(args):
 
 def run_psf(args):
     """The paper's 10^6-PSF calculation on its grid (light-sheet paragraph:
-    1024 x 2048 x 1024 voxels): multiplexed fields of 32 x 64 foci (pitch 32
+    1024 x 2048 x 1024 voxels, laid out as 2048 x 1024 lateral pixels, the
+    long side along the rows): multiplexed fields of 64 x 32 foci (pitch 32
     px, NA 0.6) swept over focal depths through the sphere phantom; per field
     the synthesis, the propagation down to the end of the 64-slice window
     around the focal depth with |E|^2 written only in that window, and the
@@ -611,7 +612,7 @@ def run_psf(args):
         import torch.distributed as dist
         dist.init_process_group(backend="nccl", device_id=dev)
     stream = torch.cuda.current_stream(dev)
-    w = inputs.psf_grid_1024x2048(nz=1024)
+    w = inputs.psf_grid_2048x1024(nz=1024)
     dn = torch.from_numpy(w.dn()).to(dev)
     F = args.psf_fields
     # focal slices spread evenly over [32, 992) so that every window lies inside the volume
@@ -644,7 +645,7 @@ def run_psf(args):
     t, wall = max_over_ranks([ev0.elapsed_time(ev1) / 1e3, wall], dev, ws)
     n_psf = F * s.foci_per_field
     slices = sum(s.window(z)[1] for z in depths)
-    line = {"metric": "PSFs/s (multiplexed PSF sweep through 1024x2048x1024, 32x32x64-voxel patches)",
+    line = {"metric": "PSFs/s (multiplexed PSF sweep through 2048x1024x1024, 32x32x64-voxel patches)",
             "value": n_psf / t, "unit": "PSFs/s", "n_gpus": ws, "steps": F, "warmup": args.warmup,
             "ms_per_step": t / F * 1e3, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -265,13 +265,17 @@ def multiplex_1024(nz: int = 1024) -> Workload:
                     n_spheres=800, foci_per_side=32, foci_NA=0.6)
 
 
-def psf_grid_1024x2048(nz: int = 1024) -> Workload:
+def psf_grid_2048x1024(nz: int = 1024) -> Workload:
     """The lateral grid of the paper's 10^6-PSF calculation (light-sheet
-    paragraph: 1024 x 2048 x 1024 voxels): nx = 1024, ny = 2048, dx = dz =
-    0.1625 um, the sphere phantom recipe of the 1024^3 workload at the same
-    density (1600 spheres, seed 2)."""
-    return Workload("psf1024x2048", 1024, nz, 0.1625, input_kind="foci", seed=2,
-                    n_spheres=1600, foci_NA=0.6, ny=2048)
+    paragraph: 1024 x 2048 x 1024 voxels), laid out with its 2048-pixel side
+    along x: nx = 2048, ny = 1024, dx = dz = 0.1625 um, the sphere phantom
+    recipe of the 1024^3 workload at the same density (1600 spheres, seed 2).
+    The sweep does not depend on which lateral side is x (a random phantom
+    and a lattice of foci); with the long side along the rows, the 1024-point
+    columns take the four-step register layout and a slice is 1.25x shorter
+    (28.5 against 35.6 us)."""
+    return Workload("psf2048x1024", 2048, nz, 0.1625, input_kind="foci", seed=2,
+                    n_spheres=1600, foci_NA=0.6, ny=1024)
 
 
 BATCH_SIZES = (128, 192, 256, 384, 512)
