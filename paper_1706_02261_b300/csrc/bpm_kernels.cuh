@@ -395,9 +395,9 @@ __device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
 }
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
-// --- tagged exchange of the persistent kernel --------------------------------
-// Between the half-steps of a slice the field crosses from every CTA to every
-// other one through L2.  Instead of a team barrier before each crossing (a
+// --- tagged exchange (persistent kernel; batched teams of small instances) --
+// Between the half-steps of a slice the field crosses from every CTA of the
+// team to every other one through L2.  Instead of a team barrier before each crossing (a
 // release fence, an arrival add, a poll, then the loads: four L2 latencies in
 // a row), every element carries the parity of the half-step that wrote it in
 // the lowest mantissa bit of its real part, and each consumer polls the
@@ -408,7 +408,9 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volati
 // thread reads and writes the same positions in every half-step of its kind,
 // and every half-step writes every element), which carries the other parity.
 // Nothing else crosses between CTAs during the slice loop (the propagator,
-// twiddles and index rows are read only), so no fence is needed.  Forcing the
+// twiddles and index rows are read only), so no fence is needed; one barrier
+// with release/acquire semantics after the entrance field's forward FFT_x
+// (tag 0) makes it visible over whatever the buffer held before.  Forcing the
 // bit moves the real part by at most one unit in the last place per crossing.
 __device__ __forceinline__ void st_tagged(float2* p, float2 v, unsigned tag) {
   const unsigned long long b =
@@ -504,11 +506,11 @@ __device__ __forceinline__ bool team_barrier(const StepArgs& a, unsigned& epoch,
 // after the previous round's values arrive: the consumer's reaction time is
 // on the critical path of the slice (a back-off of 100 ns between rounds, or
 // polling one missing element before reloading the rest, measured 40 % and
-// 11 % slower at 1024 x 1024).  The wait is
-// bounded like the team barrier: when timeout_ns runs out, or another CTA has
-// recorded an error, it records kDevErrTimeout (first error wins) and returns
-// false, leaving whatever was read in v (the caller finishes its half-step on
-// it, so that the CTA's barriers stay matched, and then leaves).
+// 11 % slower at 1024 x 1024).  The wait is bounded like the team barrier:
+// when timeout_ns runs out, or another CTA has recorded an error, it records
+// kDevErrTimeout (first error wins) and returns false, leaving whatever was
+// read in v (the caller finishes its half-step on it, so that the CTA's
+// barriers stay matched, and then leaves).
 template <unsigned WANT, int P, class Slot, class Ptr>
 __device__ __forceinline__ bool load_tagged(float2* v, Slot&& slot, Ptr&& ptr, const StepArgs& a) {
 #pragma unroll
@@ -586,7 +588,7 @@ __device__ __forceinline__ void store_layout(const float2* v, float2* dst, int t
     __stcg(dst + layout_index<N, T, R>(k, t), v[k]);
   }
 }
-// ... the same layouts on the tagged field of the persistent kernel
+// ... the same layouts on the tagged field
 template <unsigned WANT, int N, int T, int R>
 __device__ __forceinline__ bool load_layout_tagged(float2* v, const float2* src, int t, const StepArgs& a) {
   return load_tagged<WANT, N / T>(
@@ -606,8 +608,8 @@ __device__ __forceinline__ void store_layout_tagged(const float2* v, float2* dst
 // a.ny when NYc is 0); each group of T threads takes one row per round.
 // Groups without a row run the transforms on zeros (so that the warp or
 // group stays converged for its barriers) and skip all memory traffic.
-// TG: the working field is the persistent kernel's tagged field (rows read
-// the column half-step's tag 1 and write tag 0; the last slice's output is
+// TG: the working field is the tagged field of the exchange (rows read the
+// column half-step's tag 1 and write tag 0; the last slice's output is
 // written plain).  Returns false when a tagged wait gave up.
 template <class C, int NYc, int MODE, bool KAPPA = false, bool PK = true, bool TG = false>
 __device__ __forceinline__ bool row_half_step(const StepArgs& a, int r0, int r1, int z, float2* s_buf,
@@ -854,8 +856,8 @@ __device__ __forceinline__ bool col_half_step_4s(const StepArgs& a, int c0, int 
         }
       }
     }
-    // in the persistent kernel (TG) a CTA barrier precedes the half-step, so
-    // the exchange buffer of its first round is free already
+    // callers with TG put a CTA barrier before the half-step, so the exchange
+    // buffer of its first round is free already
     four_step_fwd<N1, SA>(v, tw, xw, xr, TG && cb == c0);
     // conj(X H [exp(i delta G)]): the inverse FFT_y is the forward one of the
     // conjugate, and its conjugated output goes to the row half-step as it is
@@ -896,7 +898,7 @@ __device__ __forceinline__ bool col_half_step_4s(const StepArgs& a, int c0, int 
 // half-step expects conjugated data when the row configuration is one; when
 // the two differ (a rectangular grid) FLIP conjugates the columns' output
 // (FLIP 1: always; 2: when a.flip_col is set, for the per-half-step launches).
-// TG: the persistent kernel's tagged field (columns read the row half-step's
+// TG: the tagged field of the exchange (columns read the row half-step's
 // tag 0 and write tag 1); returns false when a tagged wait gave up.
 template <class C, int NXc, int MODE, int FLIP = 0, bool TG = false>
 __device__ __forceinline__ bool col_half_step(const StepArgs& a, int c0, int c1, int z, float2* s_buf,
