@@ -35,7 +35,7 @@ namespace bpmk {
 //  - LoopCfg: N = R^P with one radix R; one pass function (LoopFFT) and the
 //    inverse by conjugation, so a half-step is a loop over 2P passes with the
 //    pointwise operation (propagator or screen) in the middle, rolled (one
-//    compact copy of the pass) or unrolled (U, the 1024-point transform).
+//    compact copy of the pass) or unrolled (U; every configuration here).
 //  - GroupCfg: mixed radices (products with 3, or 2^7) through the unrolled
 //    GroupFFT with separate forward and inverse schedules.
 // Both expose: T threads per row, the register layouts L(R0) (natural order,
@@ -201,19 +201,21 @@ using Rad4x8x8 = Radices<4, 8, 8>;
 // single-field square plans, kSchedules(N) of them).
 template <int N, int S = 0>
 struct Cfg;
-template <> struct Cfg<64> : LoopCfg<64, 8, 8, 8, 73> {};
+template <> struct Cfg<64> : LoopCfg<64, 8, 8, 8, 73, true> {};
 template <> struct Cfg<96> : GroupCfg<96, 8, 109, GroupFFT<96, 8, 8, -1, Radices<4, 4, 6>>, GroupFFT<96, 8, 8, +1, Radices<6, 4, 4>>> {};
 template <> struct Cfg<128> : GroupCfg<128, 8, 145, GroupFFT<128, 8, 8, -1, Rad8x16>, GroupFFT<128, 8, 16, +1, Rad16x8>> {};
 template <> struct Cfg<192> : GroupCfg<192, 8, 219, GroupFFT<192, 8, 8, -1, Rad8x8x3>, GroupFFT<192, 8, 8, +1, Rad3x8x8>> {};
 // 256 and 512: one row per warp (32 threads, 8 or 16 points each), so a
 // single field spreads over 32 or 64 CTAs (about 1.4x and 1.7x shorter slices
-// than two rows per warp); 512 keeps the rolled radix-8 loop, whose small code
-// serves the batched kernel (where all sizes share one instruction stream)
-// better than an unrolled 16 x 16 x 2 schedule; strides from the half-warp
-// bank model
+// than two rows per warp); schedule 0 of 512 is the radix-8 loop; strides from
+// the half-warp bank model.  The radix loops (64, 256 schedule 2, 512
+// schedule 0, 1024) are unrolled: with the tagged exchange their pass-index
+// branches and twiddle address arithmetic cost more than the larger code
+// (slices 13 % shorter at 64^2, 12 % at 512^2, 8 % at 256^2, 6 % at 1024^2;
+// the batched schedule sets 0 and 2 6 % and 1 % shorter)
 template <> struct Cfg<256> : GroupCfg<256, 32, 274, GroupFFT<256, 32, 16, -1, Rad8x8x4>, GroupFFT<256, 32, 16, +1, Rad4x8x8>> {};
 template <> struct Cfg<384> : GroupCfg<384, 16, 409, GroupFFT<384, 16, 16, -1, Rad8x8x6>, GroupFFT<384, 16, 16, +1, Rad6x8x8>> {};
-template <> struct Cfg<512> : LoopCfg<512, 32, 8, 16, 546> {};
+template <> struct Cfg<512> : LoopCfg<512, 32, 8, 16, 546, true> {};
 template <> struct Cfg<768> : GroupCfg<768, 32, 818, GroupFFT<768, 32, 16, -1, Radices<8, 8, 12>>, GroupFFT<768, 32, 16, +1, Radices<12, 8, 8>>> {};
 template <> struct Cfg<1024> : FourStepCfg<LoopCfg<1024, 32, 32, 32, 1058, true>, 32> {};
 // 1536 and 2048: two warps per row or column (64 threads, 24 or 32 points
@@ -231,16 +233,16 @@ template <> struct Cfg<512, 1> : GroupCfg<512, 32, 546, GroupFFT<512, 32, 16, -1
 template <> struct Cfg<512, 2> : GroupCfg<512, 32, 546, GroupFFT<512, 32, 16, -1, Radices<16, 16, 2>>,
                                           GroupFFT<512, 32, 16, +1, Radices<2, 16, 16>>> {};
 template <> struct Cfg<256, 1> : GroupCfg<256, 32, 274, GroupFFT<256, 32, 16, -1, Rad4x8x8>, GroupFFT<256, 32, 16, +1, Rad8x8x4>> {};
-template <> struct Cfg<256, 2> : LoopCfg<256, 16, 16, 16, 273> {};
+template <> struct Cfg<256, 2> : LoopCfg<256, 16, 16, 16, 273, true> {};
 template <> struct Cfg<1024, 1> : LoopCfg<1024, 32, 32, 32, 1058, true> {};
 
 // number of schedules of length n (Cfg<n, 0> .. Cfg<n, kSchedules(n) - 1>)
 __host__ __device__ constexpr int kSchedules(int n) { return n == 256 || n == 512 ? 3 : (n == 1024 ? 2 : 1); }
 // schedule a single-field plan starts with: the fastest measured on a B300
-// (us per slice with the intensity volume: 256^2 6.80 / 6.82 / 8.84,
-// 512^2 10.91 / 10.28 / 9.86, 1024^2 14.15 / 16.14); batched plans always
-// use schedule 0, the one compiled into the batched kernel; the rows and
-// columns of a rectangular grid take the default of their own length
+// (us per slice with the intensity volume, tagged exchange: 256^2 4.48 /
+// 4.43 / 5.75, 512^2 7.57 / 7.54 / 7.28, 1024^2 10.6 / 13.5); batched plans
+// take schedule sets instead (bpm_autotune); the rows and columns of a
+// rectangular grid take the default of their own length
 __host__ __device__ constexpr int kDefaultSchedule(int n) { return n == 512 ? 2 : 0; }
 
 // One grid's transforms: rows of length NX = CR::N (ny of them), columns of

@@ -384,8 +384,8 @@ __device__ __forceinline__ void conj_all(float2* v, int n) {
 // serves all passes and the instruction footprint of a half-step stays a few
 // KiB (for kernels whose one instruction stream holds several sizes); with U
 // true the passes are unrolled, so that the pass index, the twiddle addresses
-// and the exchange branches are compile-time (1024 x 1024 persistent kernel:
-// 5.7 % shorter slices).
+// and the exchange branches are compile-time (every configuration uses this:
+// 6-13 % shorter slices than the rolled loop).
 template <int N_, int T_, int R_, int PAD_, bool U_ = false>
 struct LoopFFT {
   static constexpr int N = N_, T = T_, R = R_, PAD = PAD_;
