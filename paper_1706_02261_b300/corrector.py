@@ -8,7 +8,7 @@ E <- E + f(E).  Training pairs are produced by the propagation kernels
 themselves: the input is one coarse step from the fine-step field at plane 4j,
 the target is the fine-step field at plane 4j + 4, both divided by the RMS
 amplitude of the input so the network sees fields of unit size.  Fine-step BPM is both the
-fallback and the judge of the corrector's error.
+fallback and the reference the corrector's error is measured against.
 
 This module only orchestrates calls into libbpm.so (all arithmetic runs in its
 kernels); torch provides device memory and batching of tensors.
@@ -306,7 +306,7 @@ def evaluate_volume(cs: CropSetup, seed: int, corr: "B.Corrector | None", dev, d
 
 
 def choose_path(held_out_rows, gate: float = 1e-3) -> str:
-    """Fine-step BPM is the fallback and the judge: the corrected coarse path
+    """Fine-step BPM is the fallback and the reference: the corrected coarse path
     is used only when its intensity error against fine-step BPM on every
     held-out volume is within the gate, else propagation stays fine-step."""
     ok = all(r.get("corrected_intensity", np.inf) <= gate for r in held_out_rows)
